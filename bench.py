@@ -1,0 +1,387 @@
+"""Benchmark of the all-pairs PCC hot path on GB300.
+
+Workload: the output-bound configuration, n = 65,536 genes x l = 512
+samples of log2(1 + NB counts) with 200 planted 40-gene modules (FP32
+input).  One step = the whole path on one matrix resident in HBM:
+standardize (Eq. (5), FP64 row statistics) -> split tensor-core contraction
+of the upper triangle (Eq. (6)) writing the packed FP32 triangle
+(2,147,450,880 pairs, 8.59 GB) and the fused |r| >= 0.8 edge list.
+
+Metric: Gpair*samples/s = pairs(i<j) * l / time / 1e9.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle (the
+baseline this project is measured against) on bounded samples of the same
+workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GENES = 65536
+L_SAMPLES = 512
+SEED = 3
+TAU = 0.8
+EDGE_CAP = 1 << 24
+METRIC = ("all-pairs PCC Gpair·samples/s, split-TC vs plain FP32 GPU at "
+          "max|Δr|≤1e-5")
+UNIT = "Gpair*samples/s"
+WORKLOAD = "output-bound all-pairs PCC, n=65536 x l=512 FP32"
+
+
+def gpair_samples(n, l):
+    return n * (n - 1) / 2 * l / 1e9
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained",
+                                                      d["bf16_tflops"]), \
+            "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}",
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["n/a"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_rate(X, seconds: float, seed: int = 11):
+    """Time the FP64 oracle (as it stands) on a bounded random sample of the
+    workload's pairs; returns (Gpair*samples/s, cores, sample text)."""
+    import oracle
+    n, l = X.shape
+    rng = np.random.default_rng(seed)
+    X64 = X.astype(np.float64)
+    npairs = 20000
+    while True:
+        I = rng.integers(0, n, npairs)
+        J = rng.integers(0, n, npairs)
+        t0 = time.perf_counter()
+        oracle.pcc_pairs(X64, I, J)
+        dt = time.perf_counter() - t0
+        if dt >= seconds or npairs >= 1 << 28:
+            break
+        npairs = int(npairs * min(max(seconds / max(dt, 1e-3), 2.0), 64.0))
+    rate = npairs * l / dt / 1e9
+    sample = (f"{npairs} random pairs (i,j) of the {n}x{l} matrix, Eq. (1) "
+              f"in FP64 with per-row mean/SSQ, {dt:.1f} s")
+    return rate, oracle.num_threads(), sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import synth
+    X = synth.counts_log(N_GENES, L_SAMPLES, SEED)
+    per_step = max(0.5, 120.0 / max(1, args.steps + args.warmup))
+    rates = []
+    for s in range(args.warmup + args.steps):
+        r, cores, sample = oracle_rate(X, per_step, seed=100 + s)
+        if s >= args.warmup:
+            rates.append(r)
+    value = statistics.median(rates)
+    total_pairs = gpair_samples(N_GENES, L_SAMPLES)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_pairs / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_GENES, "l": L_SAMPLES,
+                   "tau": TAU, "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import paper_1605_01584_gb300 as pcc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pcc.load()
+    import synth
+    n, l = args.n, args.l
+    X = synth.counts_log(n, l, SEED + 1000 * rank)
+    Xd = torch.from_numpy(X).cuda()
+    npairs = n * (n - 1) // 2
+    R = torch.empty(npairs, dtype=torch.float32, device="cuda")
+    E = torch.empty(EDGE_CAP * pcc.EDGE_BYTES, dtype=torch.uint8,
+                    device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    Z = pcc.pcc_standardize(Xd, args.prec)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        pcc.pcc_standardize(Xd, args.prec, Z=Z)
+        if ev is not None:
+            ev[1].record(stream)
+        cnt.zero_()
+        if ev is not None:
+            ev[2].record(stream)
+        pcc.pcc_threshold_edges(Z, TAU, E, EDGE_CAP, cnt, R)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = pcc.pcc_sync_status(Z)
+    if st != 0:
+        raise RuntimeError(f"device status {pcc.pcc_status_string(st)}")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    std_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    pair_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    edges_found = int(cnt.item())
+    st = pcc.pcc_sync_status(Z)
+    if st != 0:
+        raise RuntimeError(f"device status {pcc.pcc_status_string(st)}")
+
+    ms_step = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = gpair_samples(n, l) * world / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (the fused pair kernel)
+    hbm, bf16, bf16_sus, peak_kind = peaks()
+    info = Z.info()
+    z_bytes = n * info["lpad"] * 2 * (1 if args.prec == "bf16x1" else 2)
+    alg_bytes = npairs * 4 + z_bytes + n + min(edges_found, EDGE_CAP) * 12
+    pair_avg = statistics.mean(pair_ms)
+    achieved_gbs = alg_bytes / (pair_avg / 1e3) / 1e9
+    alg_flops = 2.0 * npairs * l
+    nprod = 1 if args.prec == "bf16x1" else 3
+    exec_flops = nprod * 2.0 * (info["lpad"]) * 128 * 256 * 2 * (
+        (-(-n // 256)) * (-(-n // 256) + 1) // 2)
+    exec_tflops = exec_flops / (pair_avg / 1e3) / 1e12
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16", "fp16x3s": "f16",
+                  "bf16x1": "bf16"}.get(args.prec, args.prec),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "l": l, "tau": TAU,
+                   "split": args.prec, "seed": SEED,
+                   "per_rank": "independent matrix per GPU (seed + 1000*rank)",
+                   "l2": "inputs larger than L2 (134 MB X; 8.6 GB output "
+                         "streamed per step)"},
+        "ms_standardize": statistics.mean(std_ms),
+        "ms_pairs": pair_avg,
+        "edges": edges_found,
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved_gbs / hbm,
+                     "traffic": None,
+                     "kernel": "k_pairs_tc (fused packed + edges)",
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline_split_executed": {
+            "bound": "tensor", "achieved": exec_tflops, "peak": bf16_sus,
+            "unit": "TFLOP/s", "frac": exec_tflops / bf16_sus,
+            "executed_flops_per_launch": exec_flops,
+            "algorithmic_flops_per_launch": alg_flops,
+            "peak_kind": peak_kind + " sustained bf16"},
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+    }
+
+    # plain FP32 CUDA-core comparator on the same matrix
+    if not args.skip_fp32:
+        Z32 = pcc.pcc_standardize(Xd, "fp32")
+        for _ in range(2):
+            pcc.pcc_standardize(Xd, "fp32", Z=Z32)
+            pcc.pcc_allpairs_upper(Z32, R)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record(stream)
+        for _ in range(reps):
+            pcc.pcc_standardize(Xd, "fp32", Z=Z32)
+            cnt.zero_()
+            pcc.pcc_threshold_edges(Z32, TAU, E, EDGE_CAP, cnt, R)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms32 = a.elapsed_time(b) / reps
+        out["fp32_simt"] = {"ms_per_step": ms32,
+                            "value": gpair_samples(n, l) / (ms32 / 1e3),
+                            "speedup_split_tc": ms32 / ms_step}
+        Z32.close()
+
+    # end to end through the C ABI with host buffers
+    if not args.skip_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Rh = torch.empty(npairs, dtype=torch.float32, pin_memory=True)
+        Eh = torch.empty(EDGE_CAP * pcc.EDGE_BYTES, dtype=torch.uint8,
+                         pin_memory=True)
+        ch = torch.empty(1, dtype=torch.int64, pin_memory=True)
+        e2e_steps = max(2, min(args.steps, 5))
+
+        def e2e_step():
+            Xd.copy_(Xh, non_blocking=True)
+            pcc.pcc_standardize(Xd, args.prec, Z=Z)
+            cnt.zero_()
+            pcc.pcc_threshold_edges(Z, TAU, E, EDGE_CAP, cnt, R)
+            Rh.copy_(R, non_blocking=True)
+            ch.copy_(cnt, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            ne = min(int(ch.item()), EDGE_CAP)
+            Eh[:ne * pcc.EDGE_BYTES].copy_(E[:ne * pcc.EDGE_BYTES])
+            return ne
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = 0
+        for _ in range(e2e_steps):
+            ne = e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        out["e2e"] = {"value": gpair_samples(n, l) * world / (e2e_ms / 1e3),
+                      "unit": UNIT, "ms_per_step": e2e_ms,
+                      "h2d_bytes_per_step": X.nbytes,
+                      "d2h_bytes_per_step": npairs * 4 + 8 + ne * 12}
+
+    if rank == 0 and not args.skip_cpu:
+        v, cores, sample = oracle_rate(X, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores,
+                               "kind": "oracle", "sample": sample}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="fp16x3s",
+                    choices=["bf16x3", "fp16x3s", "bf16x1"])
+    ap.add_argument("--n", type=int, default=N_GENES)
+    ap.add_argument("--l", type=int, default=L_SAMPLES)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * pcc.h -- C ABI of the GB300 all-pairs Pearson correlation library.
+ *
+ * The library computes, for an n x l matrix X of n variables (genes) with
+ * l samples each, the Pearson correlation r(i,j) of every pair of rows,
+ * Eq. (1) of LightPCC (Liu, Pan and Aluru, arXiv 1605.01584, Section I):
+ *
+ *   r(u,v) = sum_k (u_k - ubar)(v_k - vbar)
+ *            / sqrt( sum_k (u_k - ubar)^2 * sum_k (v_k - vbar)^2 )
+ *
+ * through the paper's reformulation (Section III-A, Eq. (5)-(6)): each row
+ * is centred and scaled to unit norm once, z_i = (x_i - xbar_i)/||x_i -
+ * xbar_i||, after which r(i,j) = z_i . z_j, the upper triangle of Z Z^T.
+ *
+ * Conventions shared by every entry point:
+ *   - Data pointers (X, R, edges, counts, permutations) are DEVICE pointers
+ *     owned by the caller; the library never frees them.  A pcc_zmat is
+ *     allocated by the library (pcc_standardize) and released with
+ *     pcc_zmat_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call only enqueues work on that stream and returns;
+ *     results are ready once the stream is synchronised.
+ *   - Calls return a pcc_status and never abort, trap or throw.  Errors the
+ *     GPU detects while running (a pipeline wait that exceeded its limit, an
+ *     edge list that overflowed) are recorded in a status word inside the
+ *     pcc_zmat and returned by pcc_sync_status.
+ *   - Row-major layouts with explicit leading dimensions; sizes are int64.
+ *   - Pairs are i < j (the major diagonal is excluded, Section III-B allows
+ *     this adaptation).  The packed output holds pair (i,j) at
+ *       J(i,j) = i(2n - i - 1)/2 + (j - i - 1)
+ *     (Eq. (9)-(10) of Section III-B with the diagonal removed), so the
+ *     pairs of row i are contiguous and rows follow each other.
+ *   - A row whose centred sum of squares is zero or not finite is flagged;
+ *     every r involving it is NaN (Eq. (1) gives 0/0), it never becomes an
+ *     edge and its permutation count is 0.
+ */
+#ifndef PCC_H
+#define PCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PCC_OK = 0,
+    PCC_ERR_INVALID_ARG = 1, /* bad size, pointer, range or combination */
+    PCC_ERR_CUDA = 2,        /* a CUDA runtime/driver call failed */
+    PCC_ERR_OOM = 3,         /* device allocation failed */
+    PCC_ERR_CAPACITY = 4,    /* edge list longer than its capacity */
+    PCC_ERR_TIMEOUT = 5,     /* a device pipeline wait exceeded its limit */
+    PCC_ERR_UNSUPPORTED = 6  /* no kernel for this device / combination */
+} pcc_status;
+
+/* element type of an input or output array */
+typedef enum { PCC_F32 = 0, PCC_F64 = 1 } pcc_dtype;
+
+/* how Z is stored and which pair kernel contracts it */
+typedef enum {
+    PCC_PREC_FP64 = 0,    /* Z in FP64; FP64 CUDA-core pair kernel */
+    PCC_PREC_FP32 = 1,    /* Z in FP32; FP32 CUDA-core pair kernel */
+    PCC_PREC_BF16X3 = 2,  /* Z = hi + lo, both BF16; tensor cores run
+                             hi.hi + hi.lo + lo.hi, FP32 accumulation */
+    PCC_PREC_FP16X3S = 3, /* as BF16X3 with FP16 halves of z * 2^s,
+                             s = floor(log2(l)/2); about 30x more accurate */
+    PCC_PREC_BF16X1 = 4,  /* Z = bf16(z), one product (reported only:
+                             about 1e-3 error) */
+    PCC_PREC_AUTO = 5     /* the tuner's choice among the split forms */
+} pcc_prec;
+
+typedef struct pcc_zmat pcc_zmat; /* opaque, library-owned */
+
+/* one |r| >= tau edge, i < j, r signed (12 bytes) */
+typedef struct {
+    uint32_t i, j;
+    float r;
+} pcc_edge;
+
+/* ------------------------------------------------------------------ */
+/* Step 1: variable transformation (Eq. (5), Algorithm 3).             */
+/* ------------------------------------------------------------------ */
+
+/* Centre and scale every row of X to unit norm: per row, the mean and the
+ * centred sum of squares S are accumulated in FP64 (two passes, as
+ * Algorithm 3), then z = (x - mean)/sqrt(S) is stored in the form `prec`
+ * asks for (PCC_PREC_AUTO is resolved here).
+ *   X    device, n x l, row-major, leading dimension ldx >= l, element type
+ *        xt (PCC_F32 or PCC_F64).
+ *   *Z   if *Z is non-NULL and was made for the same device, n, l and
+ *        precision it is overwritten in place (no allocation); otherwise a
+ *        new pcc_zmat is allocated and returned in *Z (an old one is left
+ *        to the caller to destroy).
+ * Errors: PCC_ERR_INVALID_ARG for n < 2, l < 2, ldx < l, n >= 2^31, NULL X
+ * or Z; PCC_ERR_OOM; PCC_ERR_UNSUPPORTED for tensor-core forms on a device
+ * that is not sm_103. */
+pcc_status pcc_standardize(const void *X, pcc_dtype xt, int64_t n, int64_t l,
+                           int64_t ldx, pcc_prec prec, pcc_zmat **Z,
+                           void *stream);
+
+/* Free a pcc_zmat (waits for nothing: the caller must have synchronised
+ * the streams that use it).  NULL is accepted. */
+pcc_status pcc_zmat_destroy(pcc_zmat *Z);
+
+/* Shape and form of Z: n, l, padded row length lpad (elements), resolved
+ * precision, and the power-of-two exponent s of PCC_PREC_FP16X3S (0
+ * otherwise).  Any output pointer may be NULL. */
+pcc_status pcc_zmat_info(const pcc_zmat *Z, int64_t *n, int64_t *l,
+                         int64_t *lpad, int32_t *prec, int32_t *scale_exp);
+
+/* Device pointers to Z's storage (read-only views, owned by Z): hi and lo
+ * (2-byte halves, n x lpad) for the split forms, z (FP32 or FP64, n x lpad)
+ * otherwise, flags (n bytes, 1 = zero-variance or non-finite row).
+ * Pointers that do not apply are set to NULL. */
+pcc_status pcc_zmat_buffers(const pcc_zmat *Z, const void **hi,
+                            const void **lo, const void **z,
+                            const uint8_t **flags);
+
+/* ------------------------------------------------------------------ */
+/* Step 2: all pairs (Eq. (6); tiles scheduled by Eq. (16)-(19)).       */
+/* ------------------------------------------------------------------ */
+
+/* Number of work tiles of Z's pair schedule (the unit of tile ranges). */
+int64_t pcc_num_tiles(const pcc_zmat *Z);
+
+/* Packed strict upper triangle: R[J(i,j)] = r(i,j) for all i < j covered
+ * by tiles [tile_begin, tile_end) of Z's schedule (tile_end = -1 means
+ * pcc_num_tiles(Z)); other entries of R are not touched, so disjoint tile
+ * ranges can be computed by different calls, devices or ranks (Section
+ * III-D distributes equal ranges of tile ids).
+ *   R   device, n(n-1)/2 elements of type rt.  rt = PCC_F64 only for
+ *       PCC_PREC_FP64.  Tensor-core forms clamp r to [-1, 1].
+ * Errors: PCC_ERR_INVALID_ARG for NULL, a bad range or dtype. */
+pcc_status pcc_allpairs_upper(const pcc_zmat *Z, void *R, pcc_dtype rt,
+                              int64_t tile_begin, int64_t tile_end,
+                              void *stream);
+
+/* Co-expression edges: every pair with |r(i,j)| >= tau (inclusive, either
+ * sign; flagged rows never qualify) is appended to `edges` in an
+ * unspecified order, through one atomic per warp on *d_count.
+ *   edges     device, room for `capacity` records (may be NULL if
+ *             capacity == 0).
+ *   d_count   device uint64, ADDED to (the caller zeroes it first); after
+ *             the call it holds the true number of qualifying pairs even
+ *             when that exceeds capacity, in which case only `capacity` of
+ *             them are stored and pcc_sync_status reports
+ *             PCC_ERR_CAPACITY.
+ *   R         optional device FP32 packed output written in the same pass
+ *             (NULL = edges only).  Needs a tensor-core or FP32 Z. */
+pcc_status pcc_threshold_edges(const pcc_zmat *Z, float tau, pcc_edge *edges,
+                               uint64_t capacity, uint64_t *d_count,
+                               float *R, void *stream);
+
+/* Permutation test (Section IV-A): for permutations k in [k0, k1) of the P
+ * given ones, r_k(i,j) = z_i . (z_j o pi_k) with (z_j o pi_k)[s] =
+ * z_j[pi_k[s]] (only the second row of a pair is permuted); d_counts[J(i,j)]
+ * is INCREASED by #{k : |r_k(i,j)| >= |r(i,j)|}.  Counting a range and
+ * adding lets a long test be split or resumed.
+ *   d_perms   device int32, P x l, row k a permutation of 0..l-1 (not
+ *             checked on the device).
+ *   d_counts  device uint32, n(n-1)/2, packed like R.
+ * The first call on a Z allocates a work buffer kept in Z.
+ * Errors: PCC_ERR_INVALID_ARG for a bad range, NULL pointers or a non
+ * tensor-core Z. */
+pcc_status pcc_perm_test(const pcc_zmat *Z, const int32_t *d_perms,
+                         int32_t P, int32_t k0, int32_t k1,
+                         uint32_t *d_counts, void *stream);
+
+/* All pairs of B independent matrices in one persistent launch: Rs[b] is
+ * the packed FP32 triangle of Zs[b] (all Zs tensor-core forms on the same
+ * device).  The first call with a given set allocates and caches a work
+ * list. */
+pcc_status pcc_allpairs_upper_batched(const pcc_zmat *const *Zs, int32_t B,
+                                      float *const *Rs, void *stream);
+
+/* Synchronise `stream`, then return and clear the device status word of Z
+ * (PCC_OK, PCC_ERR_TIMEOUT or PCC_ERR_CAPACITY). */
+pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
+
+/* Limit, in nanoseconds, of every pipeline wait inside the tensor-core
+ * kernels (default 4e9).  A wait that runs out sets PCC_ERR_TIMEOUT in the
+ * status word and the kernel returns early instead of hanging. */
+pcc_status pcc_set_wait_limit_ns(uint64_t ns);
+
+/* ------------------------------------------------------------------ */
+/* Numbering helpers (host functions, Section III-B/C).                */
+/* ------------------------------------------------------------------ */
+
+/* n(n-1)/2, 0 for n < 2 */
+int64_t pcc_num_pairs(int64_t n);
+
+/* J(i,j) above for 0 <= i < j < n, else -1 */
+int64_t pcc_pair_index(int64_t n, int64_t i, int64_t j);
+
+/* inverse of pcc_pair_index by the closed form of Eq. (14)-(15) (with n
+ * replaced by n-1 for the strict triangle) in FP64 followed by an exact
+ * integer correction; PCC_ERR_INVALID_ARG if J is out of range */
+pcc_status pcc_pair_coords(int64_t n, int64_t J, int64_t *i, int64_t *j);
+
+/* Eq. (17)-(19): tile id Jt in [0, m(m+1)/2) -> (yt, xt), yt <= xt, by the
+ * same closed form plus correction the kernels use */
+pcc_status pcc_tile_coords(int64_t m, int64_t Jt, int64_t *yt, int64_t *xt);
+
+/* text of a status code (static storage) */
+const char *pcc_status_string(pcc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCC_H */

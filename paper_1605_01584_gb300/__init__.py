@@ -1,0 +1,263 @@
+"""Python binding of libpcc.so (include/pcc.h): all-pairs Pearson correlation
+on GB300 tensor cores.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory (tensors) and streams.  The names follow the
+C ABI; each function raises PccError when the library returns a status
+other than PCC_OK.  There is no CPU fallback: if the library is not built,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpcc.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "pcc.h")
+
+# pcc_status
+PCC_OK = 0
+PCC_ERR_INVALID_ARG = 1
+PCC_ERR_CUDA = 2
+PCC_ERR_OOM = 3
+PCC_ERR_CAPACITY = 4
+PCC_ERR_TIMEOUT = 5
+PCC_ERR_UNSUPPORTED = 6
+# pcc_dtype
+PCC_F32 = 0
+PCC_F64 = 1
+# pcc_prec
+PCC_PREC_FP64 = 0
+PCC_PREC_FP32 = 1
+PCC_PREC_BF16X3 = 2
+PCC_PREC_FP16X3S = 3
+PCC_PREC_BF16X1 = 4
+PCC_PREC_AUTO = 5
+
+PREC_NAMES = {"fp64": PCC_PREC_FP64, "fp32": PCC_PREC_FP32,
+              "bf16x3": PCC_PREC_BF16X3, "fp16x3s": PCC_PREC_FP16X3S,
+              "bf16x1": PCC_PREC_BF16X1, "auto": PCC_PREC_AUTO}
+
+EDGE_BYTES = 12  # pcc_edge {u32 i, u32 j, f32 r}
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_U64 = ctypes.c_uint64
+_ST = ctypes.c_int
+
+
+class PccError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        msg = _lib.pcc_status_string(self.status).decode() if _lib else ""
+        super().__init__(f"{where}: {msg} (status {self.status})")
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/pcc.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pcc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def load(path: str | None = None):
+    """Load libpcc.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(
+            f"{p} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(p)
+    sig = {
+        "pcc_standardize": (_ST, [_P, _I32, _I64, _I64, _I64, _I32,
+                                  ctypes.POINTER(_P), _P]),
+        "pcc_zmat_destroy": (_ST, [_P]),
+        "pcc_zmat_info": (_ST, [_P, _P, _P, _P, _P, _P]),
+        "pcc_zmat_buffers": (_ST, [_P, _P, _P, _P, _P]),
+        "pcc_num_tiles": (_I64, [_P]),
+        "pcc_allpairs_upper": (_ST, [_P, _P, _I32, _I64, _I64, _P]),
+        "pcc_threshold_edges": (_ST, [_P, ctypes.c_float, _P, _U64, _P, _P,
+                                      _P]),
+        "pcc_perm_test": (_ST, [_P, _P, _I32, _I32, _I32, _P, _P]),
+        "pcc_allpairs_upper_batched": (_ST, [_P, _I32, _P, _P]),
+        "pcc_sync_status": (_ST, [_P, _P]),
+        "pcc_set_wait_limit_ns": (_ST, [_U64]),
+        "pcc_num_pairs": (_I64, [_I64]),
+        "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
+        "pcc_pair_coords": (_ST, [_I64, _I64, _P, _P]),
+        "pcc_tile_coords": (_ST, [_I64, _I64, _P, _P]),
+        "pcc_status_string": (ctypes.c_char_p, [_ST]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != PCC_OK:
+        raise PccError(st, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _prec(p):
+    return PREC_NAMES[p] if isinstance(p, str) else int(p)
+
+
+class Zmat:
+    """Owner of a library-allocated pcc_zmat (freed on close/garbage)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def info(self):
+        n, l, lpad = _I64(), _I64(), _I64()
+        prec, s = _I32(), _I32()
+        _check(load().pcc_zmat_info(self.handle, ctypes.byref(n),
+                                    ctypes.byref(l), ctypes.byref(lpad),
+                                    ctypes.byref(prec), ctypes.byref(s)),
+               "pcc_zmat_info")
+        return dict(n=n.value, l=l.value, lpad=lpad.value, prec=prec.value,
+                    scale_exp=s.value)
+
+    def buffers(self):
+        hi, lo, z, fl = _P(), _P(), _P(), _P()
+        _check(load().pcc_zmat_buffers(self.handle, ctypes.byref(hi),
+                                       ctypes.byref(lo), ctypes.byref(z),
+                                       ctypes.byref(fl)), "pcc_zmat_buffers")
+        return dict(hi=hi.value, lo=lo.value, z=z.value, flags=fl.value)
+
+    def num_tiles(self) -> int:
+        return int(load().pcc_num_tiles(self.handle))
+
+    def close(self):
+        if self.handle and self.handle.value and _lib is not None:
+            _lib.pcc_zmat_destroy(self.handle)
+        self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pcc_standardize(X, prec="auto", Z: Zmat | None = None, stream=None,
+                    n=None, l=None, ldx=None) -> Zmat:
+    """Eq. (5): standardize the rows of the device matrix X (float32/64,
+    2-D with unit inner stride).  Reuses Z when its shape/precision match."""
+    import torch
+    L = load()
+    assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+    xt = {torch.float32: PCC_F32, torch.float64: PCC_F64}[X.dtype]
+    n = X.shape[0] if n is None else n
+    l = X.shape[1] if l is None else l
+    ldx = X.stride(0) if ldx is None else ldx
+    h = ctypes.c_void_p(Z.handle.value if Z is not None else None)
+    _check(L.pcc_standardize(_ptr(X), xt, n, l, ldx, _prec(prec),
+                             ctypes.byref(h), _stream(stream)),
+           "pcc_standardize")
+    if Z is not None and h.value == Z.handle.value:
+        return Z
+    return Zmat(h.value)
+
+
+def pcc_allpairs_upper(Z: Zmat, R, tile_begin: int = 0, tile_end: int = -1,
+                       stream=None):
+    import torch
+    rt = PCC_F64 if R.dtype == torch.float64 else PCC_F32
+    _check(load().pcc_allpairs_upper(Z.handle, _ptr(R), rt, tile_begin,
+                                     tile_end, _stream(stream)),
+           "pcc_allpairs_upper")
+    return R
+
+
+def pcc_threshold_edges(Z: Zmat, tau: float, edges, capacity: int, d_count,
+                        R=None, stream=None):
+    """edges: device buffer of >= capacity*12 bytes (or None); d_count: a
+    device int64/uint64 scalar tensor, added to."""
+    _check(load().pcc_threshold_edges(Z.handle, float(tau), _ptr(edges),
+                                      int(capacity), _ptr(d_count), _ptr(R),
+                                      _stream(stream)),
+           "pcc_threshold_edges")
+
+
+def pcc_perm_test(Z: Zmat, d_perms, P: int, k0: int, k1: int, d_counts,
+                  stream=None):
+    _check(load().pcc_perm_test(Z.handle, _ptr(d_perms), int(P), int(k0),
+                                int(k1), _ptr(d_counts), _stream(stream)),
+           "pcc_perm_test")
+
+
+def pcc_allpairs_upper_batched(Zs, Rs, stream=None):
+    B = len(Zs)
+    harr = (ctypes.c_void_p * B)(*[z.handle.value for z in Zs])
+    rarr = (ctypes.c_void_p * B)(*[r.data_ptr() for r in Rs])
+    _check(load().pcc_allpairs_upper_batched(harr, B, rarr, _stream(stream)),
+           "pcc_allpairs_upper_batched")
+
+
+def pcc_sync_status(Z: Zmat, stream=None) -> int:
+    return int(load().pcc_sync_status(Z.handle, _stream(stream)))
+
+
+def pcc_set_wait_limit_ns(ns: int):
+    _check(load().pcc_set_wait_limit_ns(int(ns)), "pcc_set_wait_limit_ns")
+
+
+def pcc_num_pairs(n: int) -> int:
+    return int(load().pcc_num_pairs(n))
+
+
+def pcc_pair_index(n: int, i: int, j: int) -> int:
+    return int(load().pcc_pair_index(n, i, j))
+
+
+def pcc_pair_coords(n: int, J: int):
+    i, j = _I64(), _I64()
+    _check(load().pcc_pair_coords(n, J, ctypes.byref(i), ctypes.byref(j)),
+           "pcc_pair_coords")
+    return i.value, j.value
+
+
+def pcc_tile_coords(m: int, Jt: int):
+    y, x = _I64(), _I64()
+    _check(load().pcc_tile_coords(m, Jt, ctypes.byref(y), ctypes.byref(x)),
+           "pcc_tile_coords")
+    return y.value, x.value
+
+
+def pcc_status_string(s: int) -> str:
+    return load().pcc_status_string(int(s)).decode()
+
+
+def edges_view(edges_u8, count: int):
+    """Split a pcc_edge byte buffer (torch uint8, on any device) into (i, j,
+    r) numpy arrays of the first `count` records."""
+    import numpy as np
+    raw = edges_u8[:count * EDGE_BYTES].cpu().numpy().view(np.uint8)
+    rec = raw.view(np.dtype([("i", "<u4"), ("j", "<u4"), ("r", "<f4")]))
+    return (rec["i"].astype(np.int64), rec["j"].astype(np.int64),
+            rec["r"].astype(np.float32))

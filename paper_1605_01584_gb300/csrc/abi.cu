@@ -1,0 +1,379 @@
+// abi.cu -- the extern "C" entry points of pcc.h: argument checks,
+// pcc_zmat allocation, TMA descriptor encoding and kernel dispatch.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "pcc_internal.h"
+#include "pcc_sched.h"
+
+namespace pcc {
+
+namespace {
+std::atomic<uint64_t> g_wait_ns{4000000000ull};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType,
+                                  cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool device_is_sm103(int dev) {
+  int maj = 0, min = 0;
+  if (cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, dev) !=
+          cudaSuccess)
+    return false;
+  return maj == 10 && min == 3;
+}
+
+pcc_prec resolve_prec(pcc_prec p) {
+  // the tuner's default for the split forms: FP16 halves with a
+  // power-of-two row scale are as fast as BF16 halves and more accurate
+  return p == PCC_PREC_AUTO ? PCC_PREC_FP16X3S : p;
+}
+
+int32_t scale_exp_for(int64_t l) {
+  // s = floor(log2(l) / 2): z * 2^s <= 2^s <= sqrt(l), so |hi| stays far
+  // from FP16 overflow while typical |z 2^s| ~ 1 keeps lo normal
+  int32_t s = 0;
+  while ((int64_t)1 << (2 * (s + 1)) <= l) ++s;
+  return s;
+}
+}  // namespace
+
+bool is_split(pcc_prec p) {
+  return p == PCC_PREC_BF16X3 || p == PCC_PREC_FP16X3S ||
+         p == PCC_PREC_BF16X1;
+}
+
+int num_sms(int device) {
+  static int cached[64] = {0};
+  if (device >= 0 && device < 64 && cached[device]) return cached[device];
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  if (v <= 0) v = 1;
+  if (device >= 0 && device < 64) cached[device] = v;
+  return v;
+}
+
+uint64_t wait_limit_ns() { return g_wait_ns.load(); }
+
+cudaError_t ensure_func_smem(const void* func, int bytes) {
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
+pcc_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PCC_OK;
+  if (e == cudaErrorMemoryAllocation) return PCC_ERR_OOM;
+  return PCC_ERR_CUDA;
+}
+
+bool encode_tmap_2d_u16(CUtensorMap* map, const void* base, int64_t rows,
+                        int64_t cols, int box_rows, bool bf16) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map,
+                  bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                  2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
+                        int64_t rows, int64_t cols, int box_rows, bool bf16) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows,
+                        (cuuint64_t)depth};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * 2,
+                           (cuuint64_t)cols * 2 * (cuuint64_t)rows};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map,
+                  bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                  3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace pcc
+
+using namespace pcc;
+
+namespace {
+
+bool zmat_matches(const pcc_zmat* Z, int dev, int64_t n, int64_t l,
+                  pcc_prec prec) {
+  return Z && Z->device == dev && Z->n == n && Z->l == l && Z->prec == prec;
+}
+
+pcc_status zmat_create(int dev, int64_t n, int64_t l, pcc_prec prec,
+                       pcc_zmat** out) {
+  pcc_zmat* Z = static_cast<pcc_zmat*>(calloc(1, sizeof(pcc_zmat)));
+  if (!Z) return PCC_ERR_OOM;
+  Z->device = dev;
+  Z->n = n;
+  Z->l = l;
+  Z->lpad = (int64_t)round_up((size_t)l, kLpadAlign);
+  Z->prec = prec;
+  Z->scale_exp = prec == PCC_PREC_FP16X3S ? scale_exp_for(l) : 0;
+  const size_t elems = (size_t)n * (size_t)Z->lpad;
+  size_t off = 0;
+  size_t off_hi = 0, off_lo = 0, off_z = 0;
+  if (is_split(prec)) {
+    off_hi = off;
+    off += round_up(elems * 2, 1024);
+    if (prec != PCC_PREC_BF16X1) {
+      off_lo = off;
+      off += round_up(elems * 2, 1024);
+    }
+  } else {
+    off_z = off;
+    off += round_up(elems * (prec == PCC_PREC_FP64 ? 8 : 4), 1024);
+  }
+  const size_t off_flags = off;
+  off += round_up((size_t)n, 256);
+  const size_t off_status = off;
+  off += 256;
+  Z->bytes = off;
+  if (cudaMalloc(&Z->base, Z->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free(Z);
+    return PCC_ERR_OOM;
+  }
+  uint8_t* b = static_cast<uint8_t*>(Z->base);
+  if (is_split(prec)) {
+    Z->hi = b + off_hi;
+    if (prec != PCC_PREC_BF16X1) Z->lo = b + off_lo;
+  } else {
+    Z->z = b + off_z;
+  }
+  Z->flags = b + off_flags;
+  Z->status = reinterpret_cast<int*>(b + off_status);
+  if (cudaMemset(Z->status, 0, 256) != cudaSuccess) {
+    cudaFree(Z->base);
+    free(Z);
+    return PCC_ERR_CUDA;
+  }
+  if (is_split(prec)) {
+    const bool bf16 = prec != PCC_PREC_FP16X3S;
+    if (!encode_tmap_2d_u16(&Z->tm_hi, Z->hi, n, Z->lpad, 128, bf16) ||
+        (Z->lo &&
+         !encode_tmap_2d_u16(&Z->tm_lo, Z->lo, n, Z->lpad, 128, bf16))) {
+      cudaFree(Z->base);
+      free(Z);
+      return PCC_ERR_CUDA;
+    }
+    if (!Z->lo) Z->tm_lo = Z->tm_hi;
+  }
+  *out = Z;
+  return PCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcc_status pcc_standardize(const void* X, pcc_dtype xt, int64_t n, int64_t l,
+                           int64_t ldx, pcc_prec prec, pcc_zmat** Z,
+                           void* stream) {
+  if (!X || !Z || n < 2 || l < 2 || ldx < l || n >= (1ll << 31) ||
+      l >= (1ll << 31) || (xt != PCC_F32 && xt != PCC_F64) ||
+      (int)prec < 0 || prec > PCC_PREC_AUTO)
+    return PCC_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PCC_ERR_CUDA;
+  const pcc_prec rp = resolve_prec(prec);
+  if (is_split(rp) && !device_is_sm103(dev)) return PCC_ERR_UNSUPPORTED;
+  if (!zmat_matches(*Z, dev, n, l, rp)) {
+    pcc_zmat* nz = nullptr;
+    pcc_status st = zmat_create(dev, n, l, rp, &nz);
+    if (st != PCC_OK) return st;
+    *Z = nz;
+  }
+  return cuda_status(launch_standardize(X, xt, ldx, *Z,
+                                        static_cast<cudaStream_t>(stream)));
+}
+
+pcc_status pcc_zmat_destroy(pcc_zmat* Z) {
+  if (!Z) return PCC_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != Z->device) cudaSetDevice(Z->device);
+  if (Z->perm_ws) cudaFree(Z->perm_ws);
+  cudaError_t e = cudaFree(Z->base);
+  if (cur != Z->device) cudaSetDevice(cur);
+  free(Z);
+  return cuda_status(e);
+}
+
+pcc_status pcc_zmat_info(const pcc_zmat* Z, int64_t* n, int64_t* l,
+                         int64_t* lpad, int32_t* prec, int32_t* scale_exp) {
+  if (!Z) return PCC_ERR_INVALID_ARG;
+  if (n) *n = Z->n;
+  if (l) *l = Z->l;
+  if (lpad) *lpad = Z->lpad;
+  if (prec) *prec = (int32_t)Z->prec;
+  if (scale_exp) *scale_exp = Z->scale_exp;
+  return PCC_OK;
+}
+
+pcc_status pcc_zmat_buffers(const pcc_zmat* Z, const void** hi,
+                            const void** lo, const void** z,
+                            const uint8_t** flags) {
+  if (!Z) return PCC_ERR_INVALID_ARG;
+  if (hi) *hi = Z->hi;
+  if (lo) *lo = Z->lo;
+  if (z) *z = Z->z;
+  if (flags) *flags = Z->flags;
+  return PCC_OK;
+}
+
+int64_t pcc_num_tiles(const pcc_zmat* Z) {
+  if (!Z) return -1;
+  if (is_split(Z->prec)) return tc_num_tiles(Z->n);
+  const int64_t t = simt_tile_size(Z->prec);
+  const int64_t m = (Z->n + t - 1) / t;
+  return m * (m + 1) / 2;
+}
+
+pcc_status pcc_allpairs_upper(const pcc_zmat* Z, void* R, pcc_dtype rt,
+                              int64_t tile_begin, int64_t tile_end,
+                              void* stream) {
+  if (!Z || !R) return PCC_ERR_INVALID_ARG;
+  const int64_t T = pcc_num_tiles(Z);
+  if (tile_end < 0) tile_end = T;
+  if (tile_begin < 0 || tile_begin > tile_end || tile_end > T)
+    return PCC_ERR_INVALID_ARG;
+  if (rt != PCC_F32 && rt != PCC_F64) return PCC_ERR_INVALID_ARG;
+  if (rt == PCC_F64 && Z->prec != PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (is_split(Z->prec))
+    return cuda_status(launch_tc_pairs(Z, static_cast<float*>(R), tile_begin,
+                                       tile_end, false, 0.f, nullptr, 0,
+                                       nullptr, s));
+  return cuda_status(launch_simt_pairs(Z, R, rt, tile_begin, tile_end, 0.f,
+                                       nullptr, 0, nullptr, s));
+}
+
+pcc_status pcc_threshold_edges(const pcc_zmat* Z, float tau, pcc_edge* edges,
+                               uint64_t capacity, uint64_t* d_count, float* R,
+                               void* stream) {
+  if (!Z || !d_count || (capacity > 0 && !edges) || !(tau >= 0.f) ||
+      !isfinite(tau))
+    return PCC_ERR_INVALID_ARG;
+  if (R && Z->prec == PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d_count);
+  const int64_t T = pcc_num_tiles(Z);
+  if (is_split(Z->prec))
+    return cuda_status(
+        launch_tc_pairs(Z, R, 0, T, true, tau, edges, capacity, cnt, s));
+  return cuda_status(launch_simt_pairs(Z, R, PCC_F32, 0, T, tau, edges,
+                                       capacity, cnt, s));
+}
+
+pcc_status pcc_perm_test(const pcc_zmat* Z, const int32_t* d_perms, int32_t P,
+                         int32_t k0, int32_t k1, uint32_t* d_counts,
+                         void* stream) {
+  (void)Z; (void)d_perms; (void)P; (void)k0; (void)k1; (void)d_counts;
+  (void)stream;
+  return PCC_ERR_UNSUPPORTED;
+}
+
+pcc_status pcc_allpairs_upper_batched(const pcc_zmat* const* Zs, int32_t B,
+                                      float* const* Rs, void* stream) {
+  (void)Zs; (void)B; (void)Rs; (void)stream;
+  return PCC_ERR_UNSUPPORTED;
+}
+
+pcc_status pcc_sync_status(pcc_zmat* Z, void* stream) {
+  if (!Z) return PCC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return PCC_ERR_CUDA;
+  int v = 0;
+  e = cudaMemcpy(&v, Z->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return PCC_ERR_CUDA;
+  if (v != 0) cudaMemset(Z->status, 0, sizeof(int));
+  return (pcc_status)v;
+}
+
+pcc_status pcc_set_wait_limit_ns(uint64_t ns) {
+  if (ns == 0) return PCC_ERR_INVALID_ARG;
+  g_wait_ns.store(ns);
+  return PCC_OK;
+}
+
+int64_t pcc_num_pairs(int64_t n) { return n < 2 ? 0 : n * (n - 1) / 2; }
+
+int64_t pcc_pair_index(int64_t n, int64_t i, int64_t j) {
+  if (i < 0 || j <= i || j >= n) return -1;
+  return pair_row_base(n, i) + j;
+}
+
+pcc_status pcc_pair_coords(int64_t n, int64_t J, int64_t* i, int64_t* j) {
+  if (!i || !j || n < 2 || J < 0 || J >= pcc_num_pairs(n))
+    return PCC_ERR_INVALID_ARG;
+  int64_t y, x;
+  tri_coords(n - 1, J, &y, &x);
+  *i = y;
+  *j = x + 1;
+  return PCC_OK;
+}
+
+pcc_status pcc_tile_coords(int64_t m, int64_t Jt, int64_t* yt, int64_t* xt) {
+  if (!yt || !xt || m < 1 || Jt < 0 || Jt >= m * (m + 1) / 2)
+    return PCC_ERR_INVALID_ARG;
+  tri_coords(m, Jt, yt, xt);
+  return PCC_OK;
+}
+
+const char* pcc_status_string(pcc_status s) {
+  switch (s) {
+    case PCC_OK: return "ok";
+    case PCC_ERR_INVALID_ARG: return "invalid argument";
+    case PCC_ERR_CUDA: return "CUDA error";
+    case PCC_ERR_OOM: return "out of device memory";
+    case PCC_ERR_CAPACITY: return "edge list capacity exceeded";
+    case PCC_ERR_TIMEOUT: return "device pipeline wait timed out";
+    case PCC_ERR_UNSUPPORTED: return "unsupported device or combination";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

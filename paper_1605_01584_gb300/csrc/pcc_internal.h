@@ -1,0 +1,69 @@
+// pcc_internal.h -- library-private declarations shared by the .cu files.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pcc.h"
+
+// Library-owned standardized matrix (Eq. (5)): one device allocation holds
+// the row data, the per-row flags and the device status word.
+struct pcc_zmat {
+  int device;
+  int64_t n, l, lpad;      // lpad: row length rounded up to 64 elements
+  pcc_prec prec;           // resolved (never PCC_PREC_AUTO)
+  int32_t scale_exp;       // FP16X3S: z stored as z * 2^scale_exp
+  void* base;              // the single allocation
+  size_t bytes;
+  void* hi;                // split forms: n x lpad 16-bit
+  void* lo;                // split forms with 3 products: n x lpad 16-bit
+  void* z;                 // FP32 / FP64 forms: n x lpad
+  uint8_t* flags;          // n bytes
+  int* status;             // device status word (pcc_status codes)
+  CUtensorMap tm_hi;       // TMA maps over hi/lo: box 64 x 128, 128-B swizzle
+  CUtensorMap tm_lo;
+  // permutation-test work buffer (allocated by the first pcc_perm_test)
+  void* perm_ws;
+  size_t perm_ws_bytes;
+};
+
+namespace pcc {
+
+constexpr int kLpadAlign = 64;
+
+bool is_split(pcc_prec p);
+int num_sms(int device);
+uint64_t wait_limit_ns();
+cudaError_t ensure_func_smem(const void* func, int bytes);
+pcc_status cuda_status(cudaError_t e);
+
+// TMA descriptor of a 2-D row-major 16-bit matrix rows x cols (cols a
+// multiple of 8), box 64 columns x box_rows rows, 128-B swizzle, zero fill.
+bool encode_tmap_2d_u16(CUtensorMap* map, const void* base, int64_t rows,
+                        int64_t cols, int box_rows, bool bf16);
+// 3-D variant: depth x rows x cols, box 64 x box_rows x 1.
+bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
+                        int64_t rows, int64_t cols, int box_rows, bool bf16);
+
+// K1: standardize rows of X into Z's storage.
+cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
+                               pcc_zmat* Z, cudaStream_t s);
+
+// K4/K5: CUDA-core pair kernels (FP32 / FP64 Z), tiles [t0, t1) of the
+// paper's triangular tile order.
+int simt_tile_size(pcc_prec p);
+cudaError_t launch_simt_pairs(const pcc_zmat* Z, void* R, pcc_dtype rt,
+                              int64_t t0, int64_t t1, float tau,
+                              pcc_edge* edges, uint64_t cap,
+                              unsigned long long* count, cudaStream_t s);
+
+// K2/K3: tensor-core pair kernel, tiles [t0, t1) of the banded super-tile
+// order (pcc_sched.h).
+int64_t tc_num_tiles(int64_t n);
+cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
+                            int64_t t1, bool edges_on, float tau,
+                            pcc_edge* edges, uint64_t cap,
+                            unsigned long long* count, cudaStream_t s);
+
+}  // namespace pcc

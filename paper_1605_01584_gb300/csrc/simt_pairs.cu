@@ -1,0 +1,249 @@
+// simt_pairs.cu -- K4 / K5: CUDA-core pair kernels over a standardized Z in
+// FP32 or FP64 (the plain-precision comparison path).
+//
+// Section III-C: the n x n job matrix is cut into BT x BT tiles, m =
+// ceil(n/BT); the tiles of the upper triangle (diagonal included) are
+// numbered by Eq. (16) and each block maps its id back to (yt, xt) with
+// Eq. (17)-(19) (FP64 root + integer correction, pcc_sched.h).  Within a
+// tile, r(i,j) = sum_k z_i[k] z_j[k] (Eq. (6)) for rows y in
+// [yt*BT, (yt+1)*BT) and columns x in [xt*BT, (xt+1)*BT); pairs with
+// x <= y are skipped (Algorithm 1 skips y > x; the diagonal is excluded
+// here).  Instead of one thread per column (the Xeon Phi layout), 256
+// threads each own a TT x TT register block, K is staged through shared
+// memory BK at a time with a register prefetch of the next stage.
+#include <math.h>
+
+#include "pcc_internal.h"
+#include "pcc_sched.h"
+
+namespace pcc {
+namespace {
+
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+
+template <typename T, int H>
+struct VecH;
+template <>
+struct VecH<float, 4> {
+  using type = float4;
+};
+template <>
+struct VecH<double, 2> {
+  using type = double2;
+};
+
+template <typename V, typename T>
+__device__ __forceinline__ T vget(const V& v, int q);
+template <>
+__device__ __forceinline__ float vget<float4, float>(const float4& v, int q) {
+  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
+}
+template <>
+__device__ __forceinline__ double vget<double2, double>(const double2& v,
+                                                       int q) {
+  return q == 0 ? v.x : v.y;
+}
+
+template <typename T, typename OutT, int BT, int TT, int BK, bool WRITE_R,
+          bool EDGES>
+__global__ void __launch_bounds__(256)
+    k_pairs_simt(const T* __restrict__ Z, const uint8_t* __restrict__ flags,
+                 int64_t n, int64_t lpad, int64_t m, int64_t t0,
+                 OutT* __restrict__ R, float tau, pcc_edge* __restrict__ edges,
+                 uint64_t cap, unsigned long long* __restrict__ count,
+                 int* __restrict__ status) {
+  static_assert((BT / TT) * (BT / TT) == 256, "256 threads per tile");
+  constexpr int H = TT / 2;
+  constexpr int PAD = 4;
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::W;
+  constexpr int NV = BT * BK / 256 / VW;  // vector loads per thread/operand
+  using VH = typename VecH<T, H>::type;
+
+  __shared__ __align__(16) T As[2][BK][BT + PAD];
+  __shared__ __align__(16) T Bs[2][BK][BT + PAD];
+  __shared__ uint8_t fr[BT], fc[BT];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  int64_t yt, xt;
+  tri_coords(m, t0 + (int64_t)blockIdx.x, &yt, &xt);
+  const int64_t row0 = yt * BT, col0 = xt * BT;
+
+  if (tid < BT) {
+    fr[tid] = (row0 + tid < n) ? flags[row0 + tid] : 1;
+    fc[tid] = (col0 + tid < n) ? flags[col0 + tid] : 1;
+  }
+
+  V ra[NV], rb[NV];
+  auto gload = [&](int64_t kb) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int idx = tid + 256 * v;
+      const int r = idx / (BK / VW);
+      const int kq = (idx % (BK / VW)) * VW;
+      const int64_t k = kb * BK + kq;
+      V za, zb;
+      if (row0 + r < n)
+        za = *reinterpret_cast<const V*>(Z + (row0 + r) * lpad + k);
+      else
+        za = V{};
+      if (col0 + r < n)
+        zb = *reinterpret_cast<const V*>(Z + (col0 + r) * lpad + k);
+      else
+        zb = V{};
+      ra[v] = za;
+      rb[v] = zb;
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int idx = tid + 256 * v;
+      const int r = idx / (BK / VW);
+      const int kq = (idx % (BK / VW)) * VW;
+#pragma unroll
+      for (int q = 0; q < VW; ++q) {
+        As[buf][kq + q][r] = vget<V, T>(ra[v], q);
+        Bs[buf][kq + q][r] = vget<V, T>(rb[v], q);
+      }
+    }
+  };
+
+  T acc[TT][TT];
+#pragma unroll
+  for (int a = 0; a < TT; ++a)
+#pragma unroll
+    for (int b = 0; b < TT; ++b) acc[a][b] = T(0);
+
+  const int64_t nkb = lpad / BK;
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int64_t kb = 0; kb < nkb; ++kb) {
+    const int cur = kb & 1;
+    if (kb + 1 < nkb) gload(kb + 1);
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      T a[TT], b[TT];
+      const VH a0 = *reinterpret_cast<const VH*>(&As[cur][k][ty * H]);
+      const VH a1 = *reinterpret_cast<const VH*>(&As[cur][k][BT / 2 + ty * H]);
+      const VH b0 = *reinterpret_cast<const VH*>(&Bs[cur][k][tx * H]);
+      const VH b1 = *reinterpret_cast<const VH*>(&Bs[cur][k][BT / 2 + tx * H]);
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        a[q] = vget<VH, T>(a0, q);
+        a[H + q] = vget<VH, T>(a1, q);
+        b[q] = vget<VH, T>(b0, q);
+        b[H + q] = vget<VH, T>(b1, q);
+      }
+#pragma unroll
+      for (int i = 0; i < TT; ++i)
+#pragma unroll
+        for (int j = 0; j < TT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    if (kb + 1 < nkb) {
+      sstore(cur ^ 1);
+      __syncthreads();
+    }
+  }
+
+  const int lane = tid & 31;
+#pragma unroll
+  for (int a = 0; a < TT; ++a) {
+    const int li = a < H ? ty * H + a : BT / 2 + ty * H + (a - H);
+    const int64_t i = row0 + li;
+    const int64_t base = pair_row_base(n, i);
+#pragma unroll
+    for (int b = 0; b < TT; ++b) {
+      const int lj = b < H ? tx * H + b : BT / 2 + tx * H + (b - H);
+      const int64_t j = col0 + lj;
+      const bool valid = (i < n) && (j < n) && (j > i);
+      const bool flagged = (fr[li] | fc[lj]) != 0;
+      T v = acc[a][b];
+      v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
+      if (flagged) v = T(NAN);
+      if constexpr (WRITE_R) {
+        if (valid) R[base + j] = (OutT)v;
+      }
+      if constexpr (EDGES) {
+        const bool e = valid && !flagged && fabs((double)v) >= (double)tau;
+        const unsigned mask = __ballot_sync(0xffffffffu, e);
+        if (mask) {
+          const int leader = __ffs(mask) - 1;
+          unsigned long long basei = 0;
+          if (lane == leader)
+            basei = atomicAdd(count, (unsigned long long)__popc(mask));
+          basei = __shfl_sync(0xffffffffu, basei, leader);
+          if (e) {
+            const unsigned long long idx =
+                basei + __popc(mask & ((1u << lane) - 1u));
+            if (idx < cap) {
+              edges[idx].i = (uint32_t)i;
+              edges[idx].j = (uint32_t)j;
+              edges[idx].r = (float)v;
+            } else {
+              atomicCAS(status, 0, (int)PCC_ERR_CAPACITY);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <typename T, typename OutT, int BT, int TT>
+cudaError_t launch_t(const pcc_zmat* Z, OutT* R, int64_t t0, int64_t t1,
+                     bool edges_on, float tau, pcc_edge* edges, uint64_t cap,
+                     unsigned long long* count, cudaStream_t s) {
+  const int64_t m = (Z->n + BT - 1) / BT;
+  const int64_t nblocks = t1 - t0;
+  if (nblocks <= 0) return cudaSuccess;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const T* z = reinterpret_cast<const T*>(Z->z);
+  if (edges_on && R)
+    k_pairs_simt<T, OutT, BT, TT, 16, true, true><<<(unsigned)nblocks, 256, 0, s>>>(
+        z, Z->flags, Z->n, Z->lpad, m, t0, R, tau, edges, cap, count, Z->status);
+  else if (edges_on)
+    k_pairs_simt<T, OutT, BT, TT, 16, false, true><<<(unsigned)nblocks, 256, 0, s>>>(
+        z, Z->flags, Z->n, Z->lpad, m, t0, R, tau, edges, cap, count, Z->status);
+  else
+    k_pairs_simt<T, OutT, BT, TT, 16, true, false><<<(unsigned)nblocks, 256, 0, s>>>(
+        z, Z->flags, Z->n, Z->lpad, m, t0, R, tau, edges, cap, count, Z->status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int simt_tile_size(pcc_prec p) { return p == PCC_PREC_FP64 ? 64 : 128; }
+
+cudaError_t launch_simt_pairs(const pcc_zmat* Z, void* R, pcc_dtype rt,
+                              int64_t t0, int64_t t1, float tau,
+                              pcc_edge* edges, uint64_t cap,
+                              unsigned long long* count, cudaStream_t s) {
+  const bool edges_on = count != nullptr;
+  if (Z->prec == PCC_PREC_FP32)
+    return launch_t<float, float, 128, 8>(Z, reinterpret_cast<float*>(R), t0,
+                                          t1, edges_on, tau, edges, cap,
+                                          count, s);
+  if (rt == PCC_F64)
+    return launch_t<double, double, 64, 4>(Z, reinterpret_cast<double*>(R),
+                                           t0, t1, edges_on, tau, edges, cap,
+                                           count, s);
+  return launch_t<double, float, 64, 4>(Z, reinterpret_cast<float*>(R), t0,
+                                        t1, edges_on, tau, edges, cap, count,
+                                        s);
+}
+
+}  // namespace pcc

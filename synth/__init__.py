@@ -69,7 +69,7 @@ def module_assignment(n: int, n_modules: int, module_size: int,
 def counts_log(n: int, l: int, seed: int, n_modules: int = 200,
                module_size: int = 40, dispersion: float = 0.2,
                meanlog: float = 3.0, sdlog: float = 1.5,
-               dtype=np.float32) -> np.ndarray:
+               dtype=np.float32, return_modules: bool = False):
     """log2(1 + count) + a_g * f_{m(g),s}.
 
     count_gs ~ NB with mean mu_g and variance mu + alpha*mu^2 (alpha =
@@ -78,7 +78,8 @@ def counts_log(n: int, l: int, seed: int, n_modules: int = 200,
     The module count is min(n_modules, n // 80).  All-zero count rows are
     kept: with no module they are constant rows (zero variance).
     Draw order: mu (n), counts (n x l), module assignment, loadings (n),
-    factors (n_modules x l)."""
+    factors (n_modules x l).  With return_modules, also returns the module
+    id of every gene (-1 = none)."""
     rng = _rng(seed)
     mu = rng.lognormal(meanlog, sdlog, size=n)
     size = 1.0 / dispersion
@@ -92,7 +93,8 @@ def counts_log(n: int, l: int, seed: int, n_modules: int = 200,
     sel = mod >= 0
     if n_mod > 0:
         x[sel] += a[sel, None] * f[mod[sel]]
-    return np.ascontiguousarray(x.astype(dtype))
+    x = np.ascontiguousarray(x.astype(dtype))
+    return (x, mod) if return_modules else x
 
 
 def uniform01(n: int, l: int, seed: int, dtype=np.float32) -> np.ndarray:
