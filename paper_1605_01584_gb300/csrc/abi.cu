@@ -93,18 +93,20 @@ pcc_status cuda_status(cudaError_t e) {
 }
 
 bool encode_tmap_2d_u16(CUtensorMap* map, const void* base, int64_t rows,
-                        int64_t cols, int box_rows, bool bf16) {
+                        int64_t cols, int box_rows, int box_cols, bool bf16) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
+  if (!fn || (box_cols != 64 && box_cols != 32)) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map,
                   bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                   2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -191,14 +193,20 @@ pcc_status zmat_create(int dev, int64_t n, int64_t l, pcc_prec prec,
   }
   if (is_split(prec)) {
     const bool bf16 = prec != PCC_PREC_FP16X3S;
-    if (!encode_tmap_2d_u16(&Z->tm_hi, Z->hi, n, Z->lpad, 128, bf16) ||
+    if (!encode_tmap_2d_u16(&Z->tm_hi, Z->hi, n, Z->lpad, 128, 64, bf16) ||
+        !encode_tmap_2d_u16(&Z->tm_hi32, Z->hi, n, Z->lpad, 128, 32, bf16) ||
         (Z->lo &&
-         !encode_tmap_2d_u16(&Z->tm_lo, Z->lo, n, Z->lpad, 128, bf16))) {
+         (!encode_tmap_2d_u16(&Z->tm_lo, Z->lo, n, Z->lpad, 128, 64, bf16) ||
+          !encode_tmap_2d_u16(&Z->tm_lo32, Z->lo, n, Z->lpad, 128, 32,
+                              bf16)))) {
       cudaFree(Z->base);
       free(Z);
       return PCC_ERR_CUDA;
     }
-    if (!Z->lo) Z->tm_lo = Z->tm_hi;
+    if (!Z->lo) {
+      Z->tm_lo = Z->tm_hi;
+      Z->tm_lo32 = Z->tm_hi32;
+    }
   }
   *out = Z;
   return PCC_OK;

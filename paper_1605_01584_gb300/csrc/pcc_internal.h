@@ -23,6 +23,8 @@ struct pcc_zmat {
   int* status;             // device status word (pcc_status codes)
   CUtensorMap tm_hi;       // TMA maps over hi/lo: box 64 x 128, 128-B swizzle
   CUtensorMap tm_lo;
+  CUtensorMap tm_hi32;     // the same with box 32 x 128, 64-B swizzle
+  CUtensorMap tm_lo32;
   // permutation-test work buffer (allocated by the first pcc_perm_test)
   void* perm_ws;
   size_t perm_ws_bytes;
@@ -39,9 +41,10 @@ cudaError_t ensure_func_smem(const void* func, int bytes);
 pcc_status cuda_status(cudaError_t e);
 
 // TMA descriptor of a 2-D row-major 16-bit matrix rows x cols (cols a
-// multiple of 8), box 64 columns x box_rows rows, 128-B swizzle, zero fill.
+// multiple of 8), box box_cols (64 or 32) columns x box_rows rows, swizzle of
+// 2*box_cols bytes, zero fill out of bounds.
 bool encode_tmap_2d_u16(CUtensorMap* map, const void* base, int64_t rows,
-                        int64_t cols, int box_rows, bool bf16);
+                        int64_t cols, int box_rows, int box_cols, bool bf16);
 // 3-D variant: depth x rows x cols, box 64 x box_rows x 1.
 bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
                         int64_t rows, int64_t cols, int box_rows, bool bf16);

@@ -70,7 +70,7 @@ __device__ __forceinline__ void wait_fail(const WaitCtx& w, int code) {
 
 // Wait for the phase of parity `parity` of `bar`; false on abort/timeout.
 __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                       const WaitCtx& w) {
+                                       const WaitCtx w) {
   if (mbar_try_wait(bar, parity)) return true;
   uint64_t t0 = global_timer_ns();
   for (uint32_t spin = 1;; ++spin) {
@@ -102,6 +102,57 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* m,
       "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0),
       "r"(c1)
       : "memory");
+}
+
+// L2 policy that keeps lines resident ahead of evict-first traffic.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;"
+               : "=l"(pol));
+  return pol;
+}
+
+// 2-D tiled load with an L2 cache-policy hint.
+__device__ __forceinline__ void tma_load_2d_hint(void* dst,
+                                                 const CUtensorMap* m,
+                                                 uint64_t* bar, int32_t c0,
+                                                 int32_t c1, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_"
+      "tx::bytes.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0),
+      "r"(c1), "l"(pol)
+      : "memory");
+}
+
+// 2-D tiled load delivered to every CTA of `mask` in the cluster (same
+// shared-memory offset for the data and the mbarrier in each of them).
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* m,
+                                               uint64_t* bar, int32_t c0,
+                                               int32_t c1, uint16_t mask,
+                                               uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_"
+      "tx::bytes.multicast::cluster.L2::cache_hint [%0], [%1, {%3, %4}], [%2], "
+      "%5, %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0),
+      "r"(c1), "h"(mask), "l"(pol)
+      : "memory");
+}
+
+// All threads of all CTAs of the cluster (release/acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::
+          : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* m,
@@ -167,6 +218,16 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
+// As umma_commit, arriving on the mbarrier at the same offset in every CTA
+// of `mask`.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster."
+      "multicast::cluster.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 // 32 lanes x 32 consecutive 32-bit columns: thread t of the warp receives
 // lane (base_lane + t), columns [col, col+32).
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr,
@@ -191,21 +252,24 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile stored the way
-// a TMA load with 128-byte swizzle writes it: rows of 128 B (64 16-bit
-// elements), 8-row groups 1024 B apart, tile base 1024-B aligned.
+// a TMA load with SWZ-byte swizzle (SWZ = 128 or 64) writes it: rows of SWZ
+// bytes (SWZ/2 16-bit elements), 8-row groups 8*SWZ bytes apart, tile base
+// aligned to 8*SWZ bytes.
 //   bits  0-13 start address >> 4     bits 16-29 leading offset >> 4 (unused
 //   bits 32-45 stride offset >> 4     for swizzled K-major; set to 1)
 //   bits 46-48 = 0b001 (sm_100 descriptor version)
-//   bits 61-63 = 2 (128-byte swizzle)
-// Advancing K by 16 elements inside the 128-B row = +32 B on the start
-// address (the swizzle is a function of the address bits).
-__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+//   bits 61-63 swizzle mode (2 = 128-byte, 4 = 64-byte)
+// Advancing K by 16 elements inside a row = +32 B on the start address (the
+// swizzle is a function of the address bits).
+template <int SWZ>
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+  static_assert(SWZ == 128 || SWZ == 64, "supported swizzles");
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)1u << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)((8u * SWZ) >> 4) << 32;
   d |= (uint64_t)1u << 46;
-  d |= (uint64_t)2u << 61;
+  d |= (uint64_t)(SWZ == 128 ? 2u : 4u) << 61;
   return d;
 }
 

@@ -13,7 +13,7 @@
 // columns.  A persistent grid (one CTA per SM) strides over the units, as
 // Algorithm 1 strides thread groups over tile ids.
 //
-// CTA roles (192 threads):
+// CTA roles (320 threads):
 //   warp 0      TMA producer: per K block of 64, loads A = rows of the unit
 //               (hi, lo: 128 x 64 each) and B = its columns (hi, lo: 256 x
 //               64 each) into a ring of shared-memory stages (128-B swizzle).
@@ -22,18 +22,24 @@
 //               (M = 128, N = 256, K = 16 per instruction), committing each
 //               stage back to the producer and each finished accumulator to
 //               the epilogue.
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
-//               lanes 32*(w%4)..+31 = its 32 rows), a transpose through
+//   warps 2-9   epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//               lanes 32*(w%4)..+31 = its 32 rows, and one half of the
+//               columns), a transpose through
 //               shared memory so that a warp stores 32 consecutive pairs of
 //               one row at a time (rows of the packed triangle are
 //               contiguous), clamp to [-1,1], NaN for flagged rows, and the
 //               optional warp-aggregated edge append.
 // The two accumulators let the epilogue of one unit overlap the MMAs of the
-// next.  Every wait is bounded (pcc_ptx.cuh): a wait that runs out records
+// next.  By default the grid is made of 2-CTA clusters: the CTAs of a pair
+// compute the two halves of one super-tile, which need the same 256 B rows,
+// so each loads 128 of them and multicasts them to both (a third less L2 to
+// shared-memory traffic); both MMAs must release a stage before either
+// producer refills it.  Every wait is bounded (pcc_ptx.cuh): a wait that runs out records
 // PCC_ERR_TIMEOUT and the CTA drains its copies, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "pcc_internal.h"
 #include "pcc_ptx.cuh"
@@ -44,12 +50,9 @@ namespace {
 
 constexpr int kBM = 128;   // rows per unit (MMA M)
 constexpr int kBN = 256;   // columns per unit (MMA N)
-constexpr int kBK = 64;    // K per stage: one 128-B swizzle row of 16-bit
 constexpr int kUK = 16;    // K per tcgen05.mma kind::f16
-constexpr int kThreads = 192;
-constexpr int kEpiWarps = 4;
-constexpr int kTileA = kBM * kBK * 2;  // 16 KB
-constexpr int kTileB = kBN * kBK * 2;  // 32 KB
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
 constexpr int kStagePad = 33;          // epilogue transpose row pitch
 constexpr int kGroupG = 8;             // super-tile rows per band
 
@@ -58,7 +61,7 @@ struct TcParams {
   int64_t m;         // super-tiles per side
   int64_t u_begin;   // units [u_begin, u_end)
   int64_t u_end;
-  int nkb;           // K blocks of 64
+  int nkb;           // K blocks of KB
   float out_scale;   // 2^-2s for FP16X3S, else 1
   float tau;
   const uint8_t* flags;
@@ -70,15 +73,22 @@ struct TcParams {
   uint64_t wait_ns;
 };
 
-template <int NPROD>
+// KB = K per ring stage: 64 (one 128-B swizzle row of 16-bit elements, 2
+// stages of 96 KB) or 32 (64-B swizzle, 4 stages of 48 KB: the same bytes in
+// flight, refilled at half the granularity).
+template <int NPROD, int KB>
 struct Cfg {
-  static constexpr int kStages = NPROD == 1 ? 4 : 2;
-  static constexpr int kStageBytes = NPROD == 1 ? (kTileA + kTileB)
-                                                : 2 * (kTileA + kTileB);
+  static constexpr int kTileA = kBM * KB * 2;
+  static constexpr int kTileB = kBN * KB * 2;
+  static constexpr int kSwz = KB * 2;  // swizzle span in bytes
+  static constexpr int kStageBytes =
+      NPROD == 1 ? (kTileA + kTileB) : 2 * (kTileA + kTileB);
+  static constexpr int kStages = (4 * 49152) / kStageBytes;
   static constexpr int kRingBytes = kStages * kStageBytes;
   static constexpr int kEpiBytes = kEpiWarps * 32 * kStagePad * 4;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmemBytes = 1024 + kRingBytes + kEpiBytes + kBarBytes;
+  static_assert(kSmemBytes <= 232448, "shared memory budget");
 };
 
 __device__ __forceinline__ void unit_coords(BandCursor* cur, const TcParams& p,
@@ -90,11 +100,13 @@ __device__ __forceinline__ void unit_coords(BandCursor* cur, const TcParams& p,
   *col0 = xt * kTcSuper;
 }
 
-template <int NPROD, bool BF16, bool WRITE_R, bool EDGES>
+template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap tm_hi,
                const __grid_constant__ CUtensorMap tm_lo, const TcParams p) {
-  using C = Cfg<NPROD>;
+  using C = Cfg<NPROD, KB>;
+  constexpr int kTileA = C::kTileA;
+  constexpr int kTileB = C::kTileB;
   constexpr int S = C::kStages;
   constexpr uint32_t kIdesc = make_idesc_f16(BF16, kBM, kBN);
 
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);  // released by the MMA of every CTA
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -149,7 +161,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // barriers of both CTAs are initialised before any multicast lands
+  if constexpr (CL == 2) cluster_sync();
   const uint32_t tmem_base = *tmem_holder;
+  const uint32_t crank = CL == 2 ? cluster_ctarank() : 0u;
 
   WaitCtx w{abort_flag, p.status, p.wait_ns};
   const int64_t n = p.n;
@@ -164,10 +179,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued_mask = 0;
       uint32_t last_phase[S];
       for (int s = 0; s < S; ++s) last_phase[s] = 0;
+      const uint64_t pol = l2_policy_evict_last();
       for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
         int64_t row0, col0;
         unit_coords(&cur, p, u, &row0, &col0);
-        if (row0 >= n) continue;
+        // a cluster's CTAs run their units in lockstep (they share B), so
+        // only the single-CTA form skips units below the last row
+        if (CL == 1 && row0 >= n) continue;
         bool ok = true;
         for (int kb = 0; kb < p.nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, w)) {
@@ -175,16 +193,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
-          const int kc = kb * kBK;
-          tma_load_2d(sA_hi(stage), &tm_hi, &full[stage], kc, (int)row0);
-          tma_load_2d(sB_hi(stage), &tm_hi, &full[stage], kc, (int)col0);
-          tma_load_2d(sB_hi(stage) + kTileA, &tm_hi, &full[stage], kc,
-                      (int)col0 + kBM);
+          const int kc = kb * KB;
+          // Z is re-read by many tiles: keep it in L2 ahead of the
+          // evict-first output stream
+          tma_load_2d_hint(sA_hi(stage), &tm_hi, &full[stage], kc, (int)row0,
+                           pol);
+          if constexpr (CL == 1) {
+            tma_load_2d_hint(sB_hi(stage), &tm_hi, &full[stage], kc,
+                             (int)col0, pol);
+            tma_load_2d_hint(sB_hi(stage) + kTileA, &tm_hi, &full[stage], kc,
+                             (int)col0 + kBM, pol);
+          } else {
+            // both CTAs need all 256 B rows: each loads its 128 and
+            // multicasts them to the pair
+            tma_load_2d_mc(sB_hi(stage) + crank * kTileA, &tm_hi,
+                           &full[stage], kc, (int)(col0 + crank * kBM), 3,
+                           pol);
+          }
           if (NPROD > 1) {
-            tma_load_2d(sA_lo(stage), &tm_lo, &full[stage], kc, (int)row0);
-            tma_load_2d(sB_lo(stage), &tm_lo, &full[stage], kc, (int)col0);
-            tma_load_2d(sB_lo(stage) + kTileA, &tm_lo, &full[stage], kc,
-                        (int)col0 + kBM);
+            tma_load_2d_hint(sA_lo(stage), &tm_lo, &full[stage], kc,
+                             (int)row0, pol);
+            if constexpr (CL == 1) {
+              tma_load_2d_hint(sB_lo(stage), &tm_lo, &full[stage], kc,
+                               (int)col0, pol);
+              tma_load_2d_hint(sB_lo(stage) + kTileA, &tm_lo, &full[stage],
+                               kc, (int)col0 + kBM, pol);
+            } else {
+              tma_load_2d_mc(sB_lo(stage) + crank * kTileA, &tm_lo,
+                             &full[stage], kc, (int)(col0 + crank * kBM), 3,
+                             pol);
+            }
           }
           issued_mask |= 1u << stage;
           last_phase[stage] = phase;
@@ -214,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
         int64_t row0, col0;
         unit_coords(&cur, p, u, &row0, &col0);
-        if (row0 >= n) continue;
+        if (CL == 1 && row0 >= n) continue;
         if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kBN);
@@ -230,19 +268,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t aL = smem_u32(sA_lo(stage));
           const uint32_t bL = smem_u32(sB_lo(stage));
 #pragma unroll
-          for (int ks = 0; ks < kBK / kUK; ++ks) {
+          for (int ks = 0; ks < KB / kUK; ++ks) {
             const uint32_t off = ks * kUK * 2;  // bytes along K
-            const uint64_t dAH = sw128_kmajor_desc(aH + off);
-            const uint64_t dBH = sw128_kmajor_desc(bH + off);
+            const uint64_t dAH = kmajor_desc<C::kSwz>(aH + off);
+            const uint64_t dBH = kmajor_desc<C::kSwz>(bH + off);
             umma_f16(d_tmem, dAH, dBH, kIdesc, (kb | ks) != 0);
             if (NPROD == 3) {
-              const uint64_t dAL = sw128_kmajor_desc(aL + off);
-              const uint64_t dBL = sw128_kmajor_desc(bL + off);
+              const uint64_t dAL = kmajor_desc<C::kSwz>(aL + off);
+              const uint64_t dBL = kmajor_desc<C::kSwz>(bL + off);
               umma_f16(d_tmem, dAH, dBL, kIdesc, 1u);
               umma_f16(d_tmem, dAL, dBH, kIdesc, 1u);
             }
           }
-          umma_commit(&empty[stage]);
+          if constexpr (CL == 1)
+            umma_commit(&empty[stage]);
+          else
+            umma_commit_mc(&empty[stage], 3);  // frees the stage in both
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -262,7 +303,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ---------------------------------------------------------- epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    // 8 warps: warp w reads TMEM lane quarter q = w % 4 (rows 32q..32q+31
+    // of the unit) and column half h (columns 128h..128h+127).
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     float* stg = epi + (warp - 2) * 32 * kStagePad;
     BandCursor cur;
     band_cursor_init(&cur, p.m, kGroupG);
@@ -271,65 +315,120 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
       int64_t row0, col0;
       unit_coords(&cur, p, u, &row0, &col0);
-      if (row0 >= n) continue;
-      if (!mbar_wait(&tfull[acc], aphase, w)) break;
-      tc_fence_after();
-      const int64_t rbase = row0 + q * 32;       // first row of this warp
+      if (CL == 1 && row0 >= n) continue;
+      const int64_t rbase = row0 + q * 32;  // first row of this warp
+      const int64_t jw0 = col0 + h * 128;   // first column of this warp
+      // flags do not depend on the accumulator: load them before waiting
       const int64_t my_i = rbase + lane;
-      const int my_flag = (my_i < n) ? p.flags[my_i] : 1;
-      const int64_t my_base = pair_row_base(n, my_i);
-#pragma unroll 1
-      for (int c = 0; c < kBN / 32; ++c) {
-        const int64_t jc0 = col0 + c * 32;
-        // warp-uniform: does this 32 x 32 block hold any pair i < j < n?
-        if (rbase >= n || jc0 >= n || jc0 + 31 <= rbase) continue;
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(
-            tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + c * 32),
-            v);
+      const int rf = (my_i < n) ? p.flags[my_i] : 1;
+      int cfl[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t jj = jw0 + c * 32 + lane;
+        cfl[c] = (jj < n) ? p.flags[jj] : 1;
+      }
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(&tfull[acc], aphase, w);
+      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+      tc_fence_after();
+      const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
+      // packed index of (rbase, 0); row i+1 starts n - i - 2 later
+      const int64_t base0 = pair_row_base(n, rbase);
+      const uint32_t t_row = tmem_base + ((uint32_t)(q * 32) << 16) +
+                             (uint32_t)(acc * kBN + h * 128);
+      // warp-uniform: does 32 x 32 block c hold any pair i < j < n?
+      auto active = [&](int c) {
+        const int64_t jc0 = jw0 + c * 32;
+        return !(rbase >= n || jc0 >= n || jc0 + 31 <= rbase);
+      };
+      auto next_active = [&](int c) {
+        ++c;
+        while (c < 4 && !active(c)) ++c;
+        return c;
+      };
+      uint32_t v[32];
+      int c = next_active(-1);
+      if (c < 4) tmem_ld_32x32b_x32(t_row + (uint32_t)(c * 32), v);
+      while (c < 4) {
         tmem_ld_wait();
 #pragma unroll
         for (int t = 0; t < 32; ++t)
           stg[lane * kStagePad + t] = __uint_as_float(v[t]);
         __syncwarp();
+        // the next block's TMEM load overlaps this block's stores
+        const int cn = next_active(c);
+        if (cn < 4) tmem_ld_32x32b_x32(t_row + (uint32_t)(cn * 32), v);
+        const int64_t jc0 = jw0 + c * 32;
         const int64_t j = jc0 + lane;
-        const int col_flag = (j < n) ? p.flags[j] : 1;
-#pragma unroll 4
-        for (int rr = 0; rr < 32; ++rr) {
-          const int64_t i = rbase + rr;
-          const int64_t base = __shfl_sync(0xffffffffu, my_base, rr);
-          const int fl = __shfl_sync(0xffffffffu, my_flag, rr) | col_flag;
-          const bool valid = (i < n) && (j < n) && (j > i);
-          float r = stg[rr * kStagePad + lane] * p.out_scale;
-          r = fminf(1.f, fmaxf(-1.f, r));
-          if (fl) r = __int_as_float(0x7fc00000);
-          if constexpr (WRITE_R) {
-            if (valid) __stcs(p.R + base + j, r);
+        const bool cflag = cfl[c] != 0;
+        const bool clean = (jc0 > rbase + 31) && (jc0 + 31 < n) &&
+                           (rbase + 31 < n) && rflags == 0 &&
+                           !__any_sync(0xffffffffu, cflag);
+        float* out = p.R + base0 + j;
+        int64_t step = n - rbase - 2;
+        bool hit = false;
+        if (clean) {
+          // every pair of the block is valid and unflagged
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr) {
+            float r = stg[rr * kStagePad + lane] * p.out_scale;
+            r = fminf(1.f, fmaxf(-1.f, r));
+            if constexpr (WRITE_R) __stcs(out, r);
+            if constexpr (EDGES) hit |= fabsf(r) >= p.tau;
+            out += step;
+            --step;
           }
-          if constexpr (EDGES) {
-            const bool e = valid && !fl && fabsf(r) >= p.tau;
-            const unsigned mask = __ballot_sync(0xffffffffu, e);
-            if (mask) {
-              const int leader = __ffs(mask) - 1;
-              unsigned long long b0 = 0;
-              if (lane == leader)
-                b0 = atomicAdd(p.count, (unsigned long long)__popc(mask));
-              b0 = __shfl_sync(0xffffffffu, b0, leader);
-              if (e) {
-                const unsigned long long idx =
-                    b0 + __popc(mask & ((1u << lane) - 1u));
-                if (idx < p.cap) {
-                  p.edges[idx].i = (uint32_t)i;
-                  p.edges[idx].j = (uint32_t)j;
-                  p.edges[idx].r = r;
-                } else {
-                  atomicCAS(p.status, 0, (int)PCC_ERR_CAPACITY);
+        } else {
+          hit = true;  // edges (if any) are handled by the scan below
+          if constexpr (WRITE_R) {
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+              const int64_t i = rbase + rr;
+              float r = stg[rr * kStagePad + lane] * p.out_scale;
+              r = fminf(1.f, fmaxf(-1.f, r));
+              if (((rflags >> rr) & 1u) || cflag)
+                r = __int_as_float(0x7fc00000);
+              if (i < n && j < n && j > i) __stcs(out, r);
+              out += step;
+              --step;
+            }
+          }
+        }
+        if constexpr (EDGES) {
+          if (__any_sync(0xffffffffu, hit)) {
+            // rare: rescan the block and append its edges, one atomic per
+            // warp and row
+            for (int rr = 0; rr < 32; ++rr) {
+              const int64_t i = rbase + rr;
+              float r = stg[rr * kStagePad + lane] * p.out_scale;
+              r = fminf(1.f, fmaxf(-1.f, r));
+              const bool fl = ((rflags >> rr) & 1u) || cflag;
+              const bool e =
+                  i < n && j < n && j > i && !fl && fabsf(r) >= p.tau;
+              const unsigned mask = __ballot_sync(0xffffffffu, e);
+              if (mask) {
+                const int leader = __ffs(mask) - 1;
+                unsigned long long b0 = 0;
+                if (lane == leader)
+                  b0 = atomicAdd(p.count, (unsigned long long)__popc(mask));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (e) {
+                  const unsigned long long idx =
+                      b0 + __popc(mask & ((1u << lane) - 1u));
+                  if (idx < p.cap) {
+                    p.edges[idx].i = (uint32_t)i;
+                    p.edges[idx].j = (uint32_t)j;
+                    p.edges[idx].r = r;
+                  } else {
+                    atomicCAS(p.status, 0, (int)PCC_ERR_CAPACITY);
+                  }
                 }
               }
             }
           }
         }
         __syncwarp();
+        c = cn;
       }
       tc_fence_before();
       __syncwarp();
@@ -342,26 +441,103 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem_base, 512);
+  // neither CTA leaves while the other may still write its shared memory
+  if constexpr (CL == 2) cluster_sync();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem_base, 512);
+  }
 }
 
-template <int NPROD, bool BF16, bool WRITE_R, bool EDGES>
+// Pairs of CTAs (2-CTA clusters) share the B operand through TMA
+// multicast; PCC_TC_CLUSTER=1 selects single CTAs.
+bool tc_use_cluster() {
+  static bool on = [] {
+    const char* e = getenv("PCC_TC_CLUSTER");
+    return !(e && atoi(e) == 1);
+  }();
+  return on;
+}
+
+template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB>
 cudaError_t launch_inst(const pcc_zmat* Z, const TcParams& p, int grid,
                         cudaStream_t s) {
-  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES>;
-  const int smem = Cfg<NPROD>::kSmemBytes;
+  const int smem = Cfg<NPROD, KB>::kSmemBytes;
+  const CUtensorMap& th = KB == 64 ? Z->tm_hi : Z->tm_hi32;
+  const CUtensorMap& tl = KB == 64 ? Z->tm_lo : Z->tm_lo32;
+  const int64_t tiles = (p.u_end - p.u_begin) / 2;
+  if (tc_use_cluster() && tiles >= 2) {
+    auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2>;
+    cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters = 0;  // per template instance
+    if (max_clusters == 0) {
+      cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
+      int mc = 0;
+      if (cudaOccupancyMaxActiveClusters(&mc, fn, &cfg) != cudaSuccess ||
+          mc <= 0) {
+        cudaGetLastError();
+        mc = num_sms(Z->device) / 2;
+      }
+      max_clusters = mc;
+    }
+    int64_t ncl = tiles < max_clusters ? tiles : max_clusters;
+    cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, fn, th, tl, p);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 1>;
   cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, kThreads, smem, s>>>(Z->tm_hi, Z->tm_lo, p);
+  fn<<<grid, kThreads, smem, s>>>(th, tl, p);
   return cudaGetLastError();
 }
 
-template <int NPROD, bool BF16>
+template <int NPROD, bool BF16, int KB>
 cudaError_t launch_prec(const pcc_zmat* Z, const TcParams& p, int grid,
                         bool write_r, bool edges_on, cudaStream_t s) {
-  if (write_r && edges_on) return launch_inst<NPROD, BF16, true, true>(Z, p, grid, s);
-  if (edges_on) return launch_inst<NPROD, BF16, false, true>(Z, p, grid, s);
-  return launch_inst<NPROD, BF16, true, false>(Z, p, grid, s);
+  if (write_r && edges_on)
+    return launch_inst<NPROD, BF16, true, true, KB>(Z, p, grid, s);
+  if (edges_on) return launch_inst<NPROD, BF16, false, true, KB>(Z, p, grid, s);
+  return launch_inst<NPROD, BF16, true, false, KB>(Z, p, grid, s);
+}
+
+template <int KB>
+cudaError_t launch_kb(const pcc_zmat* Z, TcParams& p, int grid, bool write_r,
+                      bool edges_on, cudaStream_t s) {
+  p.nkb = (int)(Z->lpad / KB);
+  switch (Z->prec) {
+    case PCC_PREC_BF16X3:
+      return launch_prec<3, true, KB>(Z, p, grid, write_r, edges_on, s);
+    case PCC_PREC_FP16X3S:
+      return launch_prec<3, false, KB>(Z, p, grid, write_r, edges_on, s);
+    case PCC_PREC_BF16X1:
+      return launch_prec<1, true, KB>(Z, p, grid, write_r, edges_on, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// K per ring stage: PCC_TC_BK=64 or 32 (default 32) selects the pipeline
+// depth; both compute the same result.
+int tc_stage_k() {
+  static int kb = [] {
+    const char* e = getenv("PCC_TC_BK");
+    return (e && atoi(e) == 64) ? 64 : 32;
+  }();
+  return kb;
 }
 
 }  // namespace
@@ -381,7 +557,6 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
   p.m = tc_super_count(Z->n);
   p.u_begin = 2 * t0;
   p.u_end = 2 * t1;
-  p.nkb = (int)(Z->lpad / kBK);
   p.out_scale = (float)ldexp(1.0, -2 * Z->scale_exp);
   p.tau = tau;
   p.flags = Z->flags;
@@ -395,16 +570,9 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
   int grid = num_sms(Z->device);
   if (units < grid) grid = (int)units;
   const bool write_r = R != nullptr;
-  switch (Z->prec) {
-    case PCC_PREC_BF16X3:
-      return launch_prec<3, true>(Z, p, grid, write_r, edges_on, s);
-    case PCC_PREC_FP16X3S:
-      return launch_prec<3, false>(Z, p, grid, write_r, edges_on, s);
-    case PCC_PREC_BF16X1:
-      return launch_prec<1, true>(Z, p, grid, write_r, edges_on, s);
-    default:
-      return cudaErrorInvalidValue;
-  }
+  if (tc_stage_k() == 64)
+    return launch_kb<64>(Z, p, grid, write_r, edges_on, s);
+  return launch_kb<32>(Z, p, grid, write_r, edges_on, s);
 }
 
 }  // namespace pcc
