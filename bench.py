@@ -62,7 +62,7 @@ def peaks():
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,"
               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,"
@@ -79,9 +79,14 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}",
                  f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark(self, which):
+        """Wall-clock bounds of the timed region (samples outside it are
+        dropped when enough fall inside)."""
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.proc is None:
@@ -92,25 +97,62 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(
+                    parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             parts[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+        os.unlink(self.path)
+        t0 = getattr(self, "t0", None)
+        t1 = getattr(self, "t1", None)
+        inside = [r for r in rows if t0 is not None and t0 <= r[0] <= t1]
+        use = inside if len(inside) >= 3 else rows
+        reasons = set()
+        for r in use:
+            for nm, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        os.unlink(self.path)
+        sm = [r[1] for r in use]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": sorted(reasons), "samples": len(use),
+                "window": "timed region" if use is inside else "whole run"}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tc_pairs.cu", "pcc_ptx.cuh", "pcc_sched.h"):
+        h.update(open(os.path.join(ROOT, "paper_1605_01584_gb300", "csrc",
+                                   f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(n, l):
+    """DRAM bytes per launch of the pair kernel from the committed ncu
+    summary, scaled to this workload; None once the kernel source differs
+    from the one the counters were taken on."""
+    p = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None, "no committed ncu capture"
+    d = json.load(open(p))
+    if d.get("kernel_src_sha") != kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    scale = (n * (n - 1) / 2) / (d["n"] * (d["n"] - 1) / 2)
+    if d.get("l") != l:
+        return None, "captured at another l"
+    return d["dram_bytes_per_launch"] * scale, (
+        f"ncu dram read+write at n={d['n']}, scaled by pairs x{scale:.2f}")
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -225,11 +267,13 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    clocks.mark("t0")
     t_start.record(stream)
     for k in range(args.steps):
         step(evs[k])
     t_end.record(stream)
     torch.cuda.synchronize()
+    clocks.mark("t1")
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -261,6 +305,7 @@ def run_gpu(args):
         (-(-n // 256)) * (-(-n // 256) + 1) // 2)
     exec_tflops = exec_flops / (pair_avg / 1e3) / 1e12
 
+    traffic, traffic_note = committed_traffic(n, l)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -278,7 +323,7 @@ def run_gpu(args):
         "edges": edges_found,
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm,
                      "unit": "GB/s", "frac": achieved_gbs / hbm,
-                     "traffic": None,
+                     "traffic": traffic, "traffic_note": traffic_note,
                      "kernel": "k_pairs_tc (fused packed + edges)",
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_bytes},
@@ -364,7 +409,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="fp16x3s",

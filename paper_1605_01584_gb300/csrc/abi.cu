@@ -113,20 +113,23 @@ bool encode_tmap_2d_u16(CUtensorMap* map, const void* base, int64_t rows,
 }
 
 bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
-                        int64_t rows, int64_t cols, int box_rows, bool bf16) {
+                        int64_t rows, int64_t cols, int box_rows, int box_cols,
+                        bool bf16) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
+  if (!fn || (box_cols != 64 && box_cols != 32)) return false;
   cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows,
                         (cuuint64_t)depth};
   cuuint64_t strides[2] = {(cuuint64_t)cols * 2,
                            (cuuint64_t)cols * 2 * (cuuint64_t)rows};
-  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map,
                   bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                   3, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -318,9 +321,11 @@ pcc_status pcc_threshold_edges(const pcc_zmat* Z, float tau, pcc_edge* edges,
 pcc_status pcc_perm_test(const pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                          int32_t k0, int32_t k1, uint32_t* d_counts,
                          void* stream) {
-  (void)Z; (void)d_perms; (void)P; (void)k0; (void)k1; (void)d_counts;
-  (void)stream;
-  return PCC_ERR_UNSUPPORTED;
+  if (!Z || !d_perms || !d_counts || P < 1 || k0 < 0 || k1 < k0 || k1 > P)
+    return PCC_ERR_INVALID_ARG;
+  if (k1 == k0) return PCC_OK;
+  return perm_test(const_cast<pcc_zmat*>(Z), d_perms, P, k0, k1, d_counts,
+                   static_cast<cudaStream_t>(stream));
 }
 
 pcc_status pcc_allpairs_upper_batched(const pcc_zmat* const* Zs, int32_t B,

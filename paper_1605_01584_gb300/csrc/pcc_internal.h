@@ -45,9 +45,10 @@ pcc_status cuda_status(cudaError_t e);
 // 2*box_cols bytes, zero fill out of bounds.
 bool encode_tmap_2d_u16(CUtensorMap* map, const void* base, int64_t rows,
                         int64_t cols, int box_rows, int box_cols, bool bf16);
-// 3-D variant: depth x rows x cols, box 64 x box_rows x 1.
+// 3-D variant: depth x rows x cols, box box_cols x box_rows x 1.
 bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
-                        int64_t rows, int64_t cols, int box_rows, bool bf16);
+                        int64_t rows, int64_t cols, int box_rows, int box_cols,
+                        bool bf16);
 
 // K1: standardize rows of X into Z's storage.
 cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
@@ -68,5 +69,10 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
                             int64_t t1, bool edges_on, float tau,
                             pcc_edge* edges, uint64_t cap,
                             unsigned long long* count, cudaStream_t s);
+
+// K6: permutation test over permutations [k0, k1) of d_perms (P x l).
+pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
+                     int32_t k0, int32_t k1, uint32_t* d_counts,
+                     cudaStream_t s);
 
 }  // namespace pcc

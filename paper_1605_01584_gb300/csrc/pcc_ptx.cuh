@@ -69,7 +69,7 @@ __device__ __forceinline__ void wait_fail(const WaitCtx& w, int code) {
 }
 
 // Wait for the phase of parity `parity` of `bar`; false on abort/timeout.
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+static __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
                                        const WaitCtx w) {
   if (mbar_try_wait(bar, parity)) return true;
   uint64_t t0 = global_timer_ns();

@@ -54,11 +54,11 @@ constexpr int kUK = 16;    // K per tcgen05.mma kind::f16
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kStagePad = 33;          // epilogue transpose row pitch
-constexpr int kGroupG = 8;             // super-tile rows per band
 
 struct TcParams {
   int64_t n;
   int64_t m;         // super-tiles per side
+  int64_t G;         // super-tile rows per band (pcc_sched.h)
   int64_t u_begin;   // units [u_begin, u_end)
   int64_t u_end;
   int nkb;           // K blocks of KB
@@ -95,7 +95,7 @@ __device__ __forceinline__ void unit_coords(BandCursor* cur, const TcParams& p,
                                             int64_t u, int64_t* row0,
                                             int64_t* col0) {
   int64_t yt, xt;
-  band_tile_coords(cur, p.m, kGroupG, u >> 1, &yt, &xt);
+  band_tile_coords(cur, p.m, p.G, u >> 1, &yt, &xt);
   *row0 = yt * kTcSuper + (u & 1) * kBM;
   *col0 = xt * kTcSuper;
 }
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------ TMA producer
     if (lane == 0) {
       BandCursor cur;
-      band_cursor_init(&cur, p.m, kGroupG);
+      band_cursor_init(&cur, p.m, p.G);
       int stage = 0;
       uint32_t phase = 0;
       uint32_t issued_mask = 0;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
       BandCursor cur;
-      band_cursor_init(&cur, p.m, kGroupG);
+      band_cursor_init(&cur, p.m, p.G);
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int h = (warp - 2) >> 2;
     float* stg = epi + (warp - 2) * 32 * kStagePad;
     BandCursor cur;
-    band_cursor_init(&cur, p.m, kGroupG);
+    band_cursor_init(&cur, p.m, p.G);
     int acc = 0;
     uint32_t aphase = 0;
     for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
@@ -449,6 +449,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Super-tile rows per band of the schedule: a band's row panels stay in L2
+// while each column panel is streamed once per band, so taller bands read
+// Z from DRAM fewer times (PCC_TC_BAND overrides the default).
+int64_t tc_band_rows() {
+  static int64_t g = [] {
+    const char* e = getenv("PCC_TC_BAND");
+    const int v = e ? atoi(e) : 0;
+    return (int64_t)(v >= 1 && v <= 1024 ? v : 32);
+  }();
+  return g;
+}
+
 // Pairs of CTAs (2-CTA clusters) share the B operand through TMA
 // multicast; PCC_TC_CLUSTER=1 selects single CTAs.
 bool tc_use_cluster() {
@@ -555,6 +567,7 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
   TcParams p;
   p.n = Z->n;
   p.m = tc_super_count(Z->n);
+  p.G = tc_band_rows();
   p.u_begin = 2 * t0;
   p.u_end = 2 * t1;
   p.out_scale = (float)ldexp(1.0, -2 * Z->scale_exp);

@@ -1,0 +1,504 @@
+// tc_perm.cu -- K6: permutation exceedance counts on the tcgen05 tensor cores.
+//
+// The permutation test motivated in Section IV-A: for permutations pi_k of
+// the l samples, r_k(i,j) = z_i . (z_j o pi_k), (z_j o pi_k)[s] =
+// z_j[pi_k[s]] (only the second row of a pair is permuted), and
+//   counts[J(i,j)] += #{k : |r_k(i,j)| >= |r(i,j)|}       for i < j.
+//
+// Two kernels per batch of permutations:
+//   k_perm_gather  writes the permuted halves ZP[k][j][s] = Z[j][pi_k[s]]
+//                  of every row for the batch into a workspace (checking each
+//                  index: an index outside [0, l) is recorded as
+//                  PCC_ERR_INVALID_ARG and read as sample 0, never out of
+//                  bounds).
+//   k_perm_tc      a persistent kernel over work items (128 x 128 tile of
+//                  the triangle, chunk of permutations).  Per item: the A
+//                  rows (z_i, hi and lo) are loaded once into shared memory
+//                  and stay resident; the unpermuted B rows give r_obs and
+//                  then each permutation's B rows (from the workspace, a 3-D
+//                  TMA map) give r_k, all as the 3-product split contraction
+//                  into a double-buffered TMEM accumulator.  The epilogue
+//                  keeps |r_obs| and 16-bit counts in registers (thread = row
+//                  i, 64 columns j) and adds the counts to the packed output
+//                  with one atomic per pair and item.
+// Same roles and bounded waits as the pair kernel (tc_pairs.cu).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdlib.h>
+
+#include "pcc_internal.h"
+#include "pcc_ptx.cuh"
+#include "pcc_sched.h"
+
+namespace pcc {
+namespace {
+
+constexpr int kPT = 128;      // tile side (MMA M = N = 128)
+constexpr int kPK = 32;       // K per stage (64-B swizzle rows)
+constexpr int kPUK = 16;
+constexpr int kPThreads = 320;
+constexpr int kPEpiWarps = 8;
+constexpr int kPTile = kPT * kPK * 2;        // 8 KB: 128 rows x 32 (16-bit)
+constexpr int kPStageB = 2 * kPTile;         // B hi + lo
+constexpr int kPMaxResidentK = 256;          // resident A up to lpad 256
+constexpr int kPSmemBudget = 232448;
+
+struct PermParams {
+  int64_t n;
+  int64_t m;          // 128-wide tiles per side
+  int64_t items;      // tiles * nchunks
+  int nchunks;        // permutation chunks per tile
+  int chunk;          // permutations per chunk
+  int kbatch;         // permutations in this batch (workspace depth)
+  int nkb;            // K blocks of 32
+  const uint8_t* flags;
+  uint32_t* counts;
+  int* status;
+  uint64_t wait_ns;
+};
+
+template <bool RESA>
+struct PCfg {
+  // resident A: nkb blocks x (hi + lo) tiles, at most kPMaxResidentK / kPK
+  static constexpr int kABytes = RESA ? (kPMaxResidentK / kPK) * 2 * kPTile : 0;
+  static constexpr int kStageBytes = RESA ? kPStageB : 2 * kPStageB;
+  static constexpr int kBarBytes = 256;
+  static constexpr int kStages =
+      (kPSmemBudget - 1024 - kABytes - kBarBytes) / kStageBytes > 8
+          ? 8
+          : (kPSmemBudget - 1024 - kABytes - kBarBytes) / kStageBytes;
+  static constexpr int kSmemBytes =
+      1024 + kABytes + kStages * kStageBytes + kBarBytes;
+  static_assert(kStages >= 2, "ring too small");
+};
+
+__global__ void __launch_bounds__(256)
+    k_perm_gather(const uint16_t* __restrict__ hi,
+                  const uint16_t* __restrict__ lo,
+                  const int32_t* __restrict__ perms, int64_t n, int64_t l,
+                  int64_t lpad, int64_t k_lo, int64_t rows_per_block,
+                  uint16_t* __restrict__ ohi, uint16_t* __restrict__ olo,
+                  int* __restrict__ status) {
+  extern __shared__ int32_t pi[];
+  const int64_t kk = blockIdx.y;
+  const int32_t* src = perms + (k_lo + kk) * l;
+  bool bad = false;
+  for (int64_t s = threadIdx.x; s < lpad; s += blockDim.x) {
+    int32_t v = s < l ? src[s] : -1;
+    if (s < l && (v < 0 || v >= l)) {
+      bad = true;
+      v = 0;
+    }
+    pi[s] = v;
+  }
+  if (bad) atomicCAS(status, 0, (int)PCC_ERR_INVALID_ARG);
+  __syncthreads();
+  const int64_t j0 = blockIdx.x * rows_per_block;
+  const int64_t j1 = j0 + rows_per_block < n ? j0 + rows_per_block : n;
+  for (int64_t j = j0; j < j1; ++j) {
+    const uint16_t* rh = hi + j * lpad;
+    const uint16_t* rl = lo + j * lpad;
+    uint16_t* oh = ohi + (kk * n + j) * lpad;
+    uint16_t* ol = olo + (kk * n + j) * lpad;
+    for (int64_t s = threadIdx.x; s < lpad; s += blockDim.x) {
+      const int32_t t = pi[s];
+      oh[s] = t >= 0 ? rh[t] : (uint16_t)0;
+      ol[s] = t >= 0 ? rl[t] : (uint16_t)0;
+    }
+  }
+}
+
+template <bool BF16, bool RESA>
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_perm_tc(const __grid_constant__ CUtensorMap tz_hi,
+              const __grid_constant__ CUtensorMap tz_lo,
+              const __grid_constant__ CUtensorMap tp_hi,
+              const __grid_constant__ CUtensorMap tp_lo, const PermParams p) {
+  using C = PCfg<RESA>;
+  constexpr int S = C::kStages;
+  constexpr uint32_t kIdesc = make_idesc_f16(BF16, kPT, kPT);
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* aregion = smem;                 // resident A (RESA)
+  uint8_t* ring = smem + C::kABytes;
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(ring + S * C::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S;
+  uint64_t* tfull = bars + 2 * S;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* afull = tempty + 2;
+  uint64_t* aempty = afull + 1;
+  uint64_t* mdone = aempty + 1;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  // stage layout: RESA: [B hi | B lo]; else [A hi | A lo | B hi | B lo]
+  auto sB_hi = [&](int s) {
+    return ring + s * C::kStageBytes + (RESA ? 0 : 2 * kPTile);
+  };
+  auto sB_lo = [&](int s) { return sB_hi(s) + kPTile; };
+  auto sA_hi = [&](int s, int kb) {
+    return RESA ? aregion + kb * 2 * kPTile : ring + s * C::kStageBytes;
+  };
+  auto sA_lo = [&](int s, int kb) { return sA_hi(s, kb) + kPTile; };
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kPEpiWarps);
+    }
+    mbar_init(afull, 1);
+    mbar_init(aempty, 1);
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_holder, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  WaitCtx w{abort_flag, p.status, p.wait_ns};
+  const int64_t n = p.n;
+
+  auto item_coords = [&](int64_t it, int64_t* row0, int64_t* col0, int* k0,
+                         int* klen) {
+    const int64_t t = it / p.nchunks;
+    const int c = (int)(it % p.nchunks);
+    int64_t yt, xt;
+    tri_coords(p.m, t, &yt, &xt);
+    *row0 = yt * kPT;
+    *col0 = xt * kPT;
+    *k0 = c * p.chunk;
+    const int e = *k0 + p.chunk < p.kbatch ? *k0 + p.chunk : p.kbatch;
+    *klen = e - *k0;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------- TMA producer
+      const uint64_t pol = l2_policy_evict_last();
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, last_phase[S];
+      for (int s = 0; s < S; ++s) last_phase[s] = 0;
+      uint32_t aph = 0;
+      bool a_issued = false;
+      uint32_t a_last = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+        int64_t row0, col0;
+        int k0, klen;
+        item_coords(it, &row0, &col0, &k0, &klen);
+        if (klen <= 0) continue;
+        if (RESA) {
+          if (!mbar_wait(aempty, aph ^ 1u, w)) break;
+          mbar_arrive_expect_tx(afull, (uint32_t)(p.nkb * 2 * kPTile));
+          a_issued = true;
+          a_last = aph;
+          for (int kb = 0; kb < p.nkb; ++kb) {
+            tma_load_2d_hint(sA_hi(0, kb), &tz_hi, afull, kb * kPK,
+                             (int)row0, pol);
+            tma_load_2d_hint(sA_lo(0, kb), &tz_lo, afull, kb * kPK,
+                             (int)row0, pol);
+          }
+          aph ^= 1u;
+        }
+        for (int pass = -1; pass < klen && ok; ++pass) {
+          for (int kb = 0; kb < p.nkb; ++kb) {
+            if (!mbar_wait(&empty[stage], phase ^ 1u, w)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
+            const int kc = kb * kPK;
+            if (!RESA) {
+              tma_load_2d_hint(sA_hi(stage, kb), &tz_hi, &full[stage], kc,
+                               (int)row0, pol);
+              tma_load_2d_hint(sA_lo(stage, kb), &tz_lo, &full[stage], kc,
+                               (int)row0, pol);
+            }
+            if (pass < 0) {
+              tma_load_2d_hint(sB_hi(stage), &tz_hi, &full[stage], kc,
+                               (int)col0, pol);
+              tma_load_2d_hint(sB_lo(stage), &tz_lo, &full[stage], kc,
+                               (int)col0, pol);
+            } else {
+              tma_load_3d(sB_hi(stage), &tp_hi, &full[stage], kc, (int)col0,
+                          k0 + pass);
+              tma_load_3d(sB_lo(stage), &tp_lo, &full[stage], kc, (int)col0,
+                          k0 + pass);
+            }
+            issued_mask |= 1u << stage;
+            last_phase[stage] = phase;
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+        }
+      }
+      WaitCtx wd = w;
+      volatile int never = 0;
+      wd.abort_flag = &never;
+      for (int s = 0; s < S; ++s)
+        if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
+      if (RESA && a_issued) mbar_wait(afull, a_last, wd);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------ MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t aphase = 0;
+      uint32_t aph = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+        int64_t row0, col0;
+        int k0, klen;
+        item_coords(it, &row0, &col0, &k0, &klen);
+        if (klen <= 0) continue;
+        if (RESA) {
+          if (!mbar_wait(afull, aph, w)) break;
+          aph ^= 1u;
+        }
+        for (int pass = -1; pass < klen && ok; ++pass) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kPT);
+          for (int kb = 0; kb < p.nkb; ++kb) {
+            if (!mbar_wait(&full[stage], phase, w)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t aH = smem_u32(sA_hi(stage, kb));
+            const uint32_t aL = smem_u32(sA_lo(stage, kb));
+            const uint32_t bH = smem_u32(sB_hi(stage));
+            const uint32_t bL = smem_u32(sB_lo(stage));
+#pragma unroll
+            for (int ks = 0; ks < kPK / kPUK; ++ks) {
+              const uint32_t off = ks * kPUK * 2;
+              const uint64_t dAH = kmajor_desc<64>(aH + off);
+              const uint64_t dBH = kmajor_desc<64>(bH + off);
+              const uint64_t dAL = kmajor_desc<64>(aL + off);
+              const uint64_t dBL = kmajor_desc<64>(bL + off);
+              umma_f16(d_tmem, dAH, dBH, kIdesc, (kb | ks) != 0);
+              umma_f16(d_tmem, dAH, dBL, kIdesc, 1u);
+              umma_f16(d_tmem, dAL, dBH, kIdesc, 1u);
+            }
+            umma_commit(&empty[stage]);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          umma_commit(&tfull[acc]);
+          acc ^= 1;
+          if (acc == 0) aphase ^= 1u;
+        }
+        // the resident A tile is free once this item's MMAs complete
+        if (RESA && ok) umma_commit(aempty);
+      }
+      umma_commit(mdone);
+      WaitCtx wd = w;
+      volatile int never = 0;
+      wd.abort_flag = &never;
+      mbar_wait(mdone, 0, wd);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;          // TMEM lane quarter: rows 32q..32q+31
+    const int h = (warp - 2) >> 2;   // columns 64h..64h+63
+    int acc = 0;
+    uint32_t aphase = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+      int64_t row0, col0;
+      int k0, klen;
+      item_coords(it, &row0, &col0, &k0, &klen);
+      if (klen <= 0) continue;
+      float robs[64];
+      uint32_t cnt[32];  // two 16-bit counts per word
+#pragma unroll
+      for (int t = 0; t < 32; ++t) cnt[t] = 0u;
+      for (int pass = -1; pass < klen; ++pass) {
+        bool got = true;
+        if (lane == 0) got = mbar_wait(&tfull[acc], aphase, w);
+        if (!__shfl_sync(0xffffffffu, got ? 1 : 0, 0)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) +
+                               (uint32_t)(acc * kPT + h * 64);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint32_t v[32];
+          tmem_ld_32x32b_x32(taddr + (uint32_t)(c * 32), v);
+          tmem_ld_wait();
+          if (pass < 0) {
+#pragma unroll
+            for (int t = 0; t < 32; ++t)
+              robs[c * 32 + t] = fabsf(__uint_as_float(v[t]));
+          } else {
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+              const uint32_t hit =
+                  fabsf(__uint_as_float(v[t])) >= robs[c * 32 + t] ? 1u : 0u;
+              cnt[c * 16 + (t >> 1)] += hit << ((t & 1) * 16);
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1u;
+      }
+      if (!ok) break;
+      // add this item's counts to the packed output
+      const int64_t i = row0 + q * 32 + lane;
+      if (i < n && p.flags[i] == 0) {
+        const int64_t base = pair_row_base(n, i);
+#pragma unroll
+        for (int t = 0; t < 64; ++t) {
+          const int64_t j = col0 + h * 64 + t;
+          const uint32_t c = (cnt[t >> 1] >> ((t & 1) * 16)) & 0xFFFFu;
+          if (c && j > i && j < n && p.flags[j] == 0)
+            atomicAdd(p.counts + base + j, c);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem_base, 512);
+  }
+}
+
+template <bool BF16, bool RESA>
+cudaError_t launch_perm_kernel(const pcc_zmat* Z, const CUtensorMap& ph,
+                               const CUtensorMap& pl, const PermParams& p,
+                               cudaStream_t s) {
+  auto fn = k_perm_tc<BF16, RESA>;
+  const int smem = PCfg<RESA>::kSmemBytes;
+  cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = num_sms(Z->device);
+  if (p.items < grid) grid = p.items;
+  fn<<<(unsigned)grid, kPThreads, smem, s>>>(Z->tm_hi32, Z->tm_lo32, ph, pl,
+                                             p);
+  return cudaGetLastError();
+}
+
+size_t perm_ws_budget() {
+  static size_t b = [] {
+    const char* e = getenv("PCC_PERM_WS_BYTES");
+    const long long v = e ? atoll(e) : 0;
+    return (size_t)(v > 0 ? v : (4ll << 30));
+  }();
+  return b;
+}
+
+}  // namespace
+
+pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
+                     int32_t k0, int32_t k1, uint32_t* d_counts,
+                     cudaStream_t s) {
+  if (Z->prec != PCC_PREC_BF16X3 && Z->prec != PCC_PREC_FP16X3S)
+    return PCC_ERR_INVALID_ARG;
+  const int64_t n = Z->n, lpad = Z->lpad;
+  const size_t per_k = (size_t)n * (size_t)lpad * 2 * 2;  // hi + lo
+  int64_t kbmax = (int64_t)(perm_ws_budget() / per_k);
+  if (kbmax < 1) kbmax = 1;
+  const int64_t total = k1 - k0;
+  const int64_t kb_alloc = total < kbmax ? total : kbmax;
+  const size_t need = per_k * (size_t)kb_alloc;
+  if (Z->perm_ws_bytes < need) {
+    if (Z->perm_ws) {
+      cudaStreamSynchronize(s);
+      cudaFree(Z->perm_ws);
+      Z->perm_ws = nullptr;
+      Z->perm_ws_bytes = 0;
+    }
+    if (cudaMalloc(&Z->perm_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return PCC_ERR_OOM;
+    }
+    Z->perm_ws_bytes = need;
+  }
+  uint16_t* wh = static_cast<uint16_t*>(Z->perm_ws);
+  const bool bf16 = Z->prec == PCC_PREC_BF16X3;
+  const int64_t m = (n + kPT - 1) / kPT;
+  const int64_t tiles = m * (m + 1) / 2;
+  const int sms = num_sms(Z->device);
+  for (int64_t kb0 = k0; kb0 < k1; kb0 += kb_alloc) {
+    const int64_t kbatch = (k1 - kb0) < kb_alloc ? (k1 - kb0) : kb_alloc;
+    uint16_t* wl = wh + (size_t)kbatch * (size_t)n * (size_t)lpad;
+    // gather the permuted halves of the batch
+    const int64_t rpb = 16;
+    dim3 g((unsigned)((n + rpb - 1) / rpb), (unsigned)kbatch, 1);
+    k_perm_gather<<<g, 256, (size_t)lpad * sizeof(int32_t), s>>>(
+        static_cast<const uint16_t*>(Z->hi),
+        static_cast<const uint16_t*>(Z->lo), d_perms, n, Z->l, lpad, kb0, rpb,
+        wh, wl, Z->status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    CUtensorMap ph, pl;
+    if (!encode_tmap_3d_u16(&ph, wh, kbatch, n, lpad, kPT, kPK, bf16) ||
+        !encode_tmap_3d_u16(&pl, wl, kbatch, n, lpad, kPT, kPK, bf16))
+      return PCC_ERR_CUDA;
+    // chunks: enough work items for about 8 per SM
+    int64_t nchunks = (8 * (int64_t)sms + tiles - 1) / tiles;
+    if (nchunks > kbatch) nchunks = kbatch;
+    if (nchunks < 1) nchunks = 1;
+    int64_t chunk = (kbatch + nchunks - 1) / nchunks;
+    if (chunk > 65535) chunk = 65535;  // 16-bit counters
+    nchunks = (kbatch + chunk - 1) / chunk;
+    PermParams p;
+    p.n = n;
+    p.m = m;
+    p.items = tiles * nchunks;
+    p.nchunks = (int)nchunks;
+    p.chunk = (int)chunk;
+    p.kbatch = (int)kbatch;
+    p.nkb = (int)(lpad / kPK);
+    p.flags = Z->flags;
+    p.counts = d_counts;
+    p.status = Z->status;
+    p.wait_ns = wait_limit_ns();
+    if (lpad <= kPMaxResidentK)
+      e = bf16 ? launch_perm_kernel<true, true>(Z, ph, pl, p, s)
+               : launch_perm_kernel<false, true>(Z, ph, pl, p, s);
+    else
+      e = bf16 ? launch_perm_kernel<true, false>(Z, ph, pl, p, s)
+               : launch_perm_kernel<false, false>(Z, ph, pl, p, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return PCC_OK;
+}
+
+}  // namespace pcc

@@ -1,0 +1,165 @@
+"""GPU parity of the permutation test (counts of |r_k| >= |r_obs|) against
+the FP64 oracle.
+
+Band rule (the reading of the comparison at a finite precision): a pair
+whose oracle |r_k| is within 1e-5 of |r_obs| for no k must have the exact
+count; otherwise the GPU count lies in [cnt_lo, cnt_hi] with cnt_lo =
+#{|r_k| >= |r_obs| + 1e-5} and cnt_hi = #{|r_k| >= |r_obs| - 1e-5}.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+BAND = 1e-5
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def gpu_perm_counts(pcc, X, perms, prec="fp16x3s", ranges=None, Z=None):
+    torch = _torch()
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    if Z is None:
+        Z = pcc.pcc_standardize(Xd, prec)
+    n = X.shape[0]
+    P = perms.shape[0]
+    dp = torch.from_numpy(np.ascontiguousarray(perms, dtype=np.int32)).cuda()
+    cnt = torch.zeros(n * (n - 1) // 2, dtype=torch.int32, device="cuda")
+    for a, b in (ranges or [(0, P)]):
+        pcc.pcc_perm_test(Z, dp, P, a, b, cnt)
+    st = pcc.pcc_sync_status(Z)
+    return cnt.cpu().numpy().astype(np.int64), st, Z
+
+
+def check_band(X, perms, got, I, J):
+    c, clo, chi = oracle.perm_counts(X, perms, I, J, delta=BAND)
+    n = X.shape[0]
+    idx = I * (2 * n - I - 1) // 2 + (J - I - 1)
+    g = got[idx]
+    exact = clo == chi
+    assert np.array_equal(g[exact], c[exact].astype(np.int64)), (
+        "exact counts differ", np.nonzero(g[exact] != c[exact])[0][:5])
+    assert np.all((g >= clo) & (g <= chi))
+    return int(exact.sum()), len(I)
+
+
+@pytest.mark.parametrize("n,l", [(130, 16), (300, 33), (257, 64),
+                                 (520, 200), (400, 256), (300, 300)])
+@pytest.mark.parametrize("prec", ["fp16x3s", "bf16x3"])
+def test_perm_counts_parity(pcc_gpu, n, l, prec):
+    X = synth.counts_log(n, l, seed=n * 7 + l)
+    X[n // 2] = 2.5  # flagged row: counts stay 0
+    perms = synth.fisher_yates_perms(40, l, seed=9)
+    got, st, _ = gpu_perm_counts(pcc_gpu, X, perms, prec)
+    assert st == 0
+    I, J = np.triu_indices(n, 1)
+    exact, tot = check_band(X, perms, got, I, J)
+    assert exact > 0.5 * tot
+    flagged = (I == n // 2) | (J == n // 2)
+    idx = I * (2 * n - I - 1) // 2 + (J - I - 1)
+    assert np.all(got[idx[flagged]] == 0)
+
+
+def test_identity_permutations_count_all(pcc_gpu):
+    X = synth.counts_log(300, 64, seed=3)
+    P = 17
+    perms = np.tile(np.arange(64, dtype=np.int32), (P, 1))
+    got, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    assert st == 0
+    _, flag = oracle.standardize(X)
+    I, J = np.triu_indices(300, 1)
+    ok = (flag[I] == 0) & (flag[J] == 0)
+    assert np.all(got[ok] == P) and np.all(got[~ok] == 0)
+
+
+def test_split_ranges_accumulate(pcc_gpu):
+    """Counting [0,a) then [a,P) adds up to counting [0,P) (resume)."""
+    X = synth.counts_log(400, 128, seed=21)
+    perms = synth.fisher_yates_perms(50, 128, seed=22)
+    whole, _, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    parts, st, _ = gpu_perm_counts(pcc_gpu, X, perms,
+                                   ranges=[(0, 13), (13, 31), (31, 50)])
+    assert st == 0
+    assert np.array_equal(whole, parts)
+
+
+def test_small_workspace_batches(pcc_gpu, tmp_path):
+    """With a workspace that holds only 3 permutations the range runs as 9
+    batches; the counts equal the single-batch run (fresh process: the
+    budget is read when the library first needs it)."""
+    import os
+    import subprocess
+    import sys
+    X = synth.counts_log(260, 96, seed=31)
+    perms = synth.fisher_yates_perms(25, 96, seed=32)
+    whole, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    assert st == 0
+    np.save(tmp_path / "x.npy", X)
+    np.save(tmp_path / "p.npy", perms)
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = (
+        "import sys, numpy as np; sys.path[:0] = [%r, %r]\n"
+        "import test_gpu_perm as t, paper_1605_01584_gb300 as pcc\n"
+        "pcc.load()\n"
+        "got, st, _ = t.gpu_perm_counts(pcc, np.load(%r), np.load(%r))\n"
+        "assert st == 0, st\n"
+        "np.save(%r, got)\n" % (here, os.path.dirname(here),
+                                 str(tmp_path / "x.npy"),
+                                 str(tmp_path / "p.npy"),
+                                 str(tmp_path / "g.npy")))
+    per_k = 260 * 128 * 4
+    env = dict(os.environ, PCC_PERM_WS_BYTES=str(3 * per_k))
+    r = subprocess.run([sys.executable, "-c", code], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert np.array_equal(np.load(tmp_path / "g.npy"), whole)
+
+
+def test_bad_permutation_index_is_reported(pcc_gpu):
+    X = synth.counts_log(200, 32, seed=5)
+    perms = synth.fisher_yates_perms(4, 32, seed=6)
+    perms[2, 7] = 32   # out of range
+    perms[3, 0] = -1
+    _, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    assert st == pcc_gpu.PCC_ERR_INVALID_ARG
+
+
+def test_invalid_ranges(pcc_gpu):
+    torch = _torch()
+    X = torch.randn((50, 16), device="cuda")
+    Z = pcc_gpu.pcc_standardize(X, "fp16x3s")
+    dp = torch.zeros((4, 16), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(50 * 49 // 2, dtype=torch.int32, device="cuda")
+    for a, b in [(-1, 2), (3, 2), (0, 5)]:
+        with pytest.raises(pcc_gpu.PccError):
+            pcc_gpu.pcc_perm_test(Z, dp, 4, a, b, cnt)
+    Z32 = pcc_gpu.pcc_standardize(X, "fp32")
+    with pytest.raises(pcc_gpu.PccError):
+        pcc_gpu.pcc_perm_test(Z32, dp, 4, 0, 4, cnt)
+
+
+def test_perm_full_config_sampled(pcc_gpu):
+    """The batched permutation workload: n=4096 x l=256, P=1000 seeded
+    Fisher-Yates permutations, checked on sampled pairs plus planted-module
+    pairs against the oracle under the band rule."""
+    n, l, P = 4096, 256, 1000
+    X, mod = synth.counts_log(n, l, seed=4, return_modules=True)
+    perms = synth.fisher_yates_perms(P, l, seed=4)
+    got, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    assert st == 0
+    rng = np.random.default_rng(104)
+    I = rng.integers(0, n, 1500)
+    J = rng.integers(0, n, 1500)
+    keep = I != J
+    I, J = np.minimum(I, J)[keep], np.maximum(I, J)[keep]
+    m0 = np.nonzero(mod == 0)[0]
+    mi, mj = np.triu_indices(len(m0), 1)
+    I = np.concatenate([I, m0[mi]])
+    J = np.concatenate([J, m0[mj]])
+    exact, tot = check_band(X, perms, got, I, J)
+    assert exact > 0.5 * tot
