@@ -173,6 +173,31 @@ pcc_status pcc_perm_test(const pcc_zmat *Z, const int32_t *d_perms,
 pcc_status pcc_allpairs_upper_batched(const pcc_zmat *const *Zs, int32_t B,
                                       float *const *Rs, void *stream);
 
+/* All pairs without any device allocation (the paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory,
+ * e.g. code running inside another framework's memory pool, programs with
+ * a device-memory budget fixed at start-up, or latency-critical paths that
+ * cannot afford cudaMalloc's implicit synchronisation).
+ * Standardizes X (device FP32, n x l, leading dimension ldx) and writes the
+ * packed FP32 triangle R (device, n(n-1)/2 floats) as pcc_standardize +
+ * pcc_allpairs_upper do, but keeps the standardized matrix in one
+ * file-scope device array of 32 MiB that every device holds from the time
+ * it loads the library until the process exits.
+ *   prec      PCC_PREC_BF16X3, PCC_PREC_FP16X3S, PCC_PREC_BF16X1 or
+ *             PCC_PREC_AUTO (tensor-core forms only).
+ *   d_status  optional device int32 (caller-owned, may be NULL) set to 0 by
+ *             the call and then to PCC_ERR_TIMEOUT if a device wait ran out.
+ * Limit: 4 * n * lpad + n (rounded up to 256) + 256 <= 32 MiB, with lpad = l
+ * rounded up to 64 (e.g. n = 16384 with l <= 448, or n = 8192 with l <=
+ * 960); larger problems return PCC_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture.  All calls
+ * on a device share the array, so calls that may overlap on the GPU (on
+ * unordered streams) race: order them on one stream. */
+pcc_status pcc_allpairs_upper_noalloc(const float *X, int64_t n, int64_t l,
+                                      int64_t ldx, pcc_prec prec, float *R,
+                                      int32_t *d_status, void *stream);
+
 /* Synchronise `stream`, then return and clear the device status word of Z
  * (PCC_OK, PCC_ERR_TIMEOUT or PCC_ERR_CAPACITY). */
 pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);

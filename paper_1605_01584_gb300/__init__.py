@@ -88,6 +88,8 @@ def load(path: str | None = None):
         "pcc_perm_test": (_ST, [_P, _P, _I32, _I32, _I32, _P, _P]),
         "pcc_allpairs_upper_batched": (_ST, [_P, _I32, _P, _P]),
         "pcc_sync_status": (_ST, [_P, _P]),
+        "pcc_allpairs_upper_noalloc": (_ST, [_P, _I64, _I64, _I64, _I32, _P,
+                                             _P, _P]),
         "pcc_set_wait_limit_ns": (_ST, [_U64]),
         "pcc_num_pairs": (_I64, [_I64]),
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
@@ -217,6 +219,18 @@ def pcc_allpairs_upper_batched(Zs, Rs, stream=None):
     rarr = (ctypes.c_void_p * B)(*[r.data_ptr() for r in Rs])
     _check(load().pcc_allpairs_upper_batched(harr, B, rarr, _stream(stream)),
            "pcc_allpairs_upper_batched")
+
+
+def pcc_allpairs_upper_noalloc(X, R, prec="auto", d_status=None,
+                               stream=None):
+    """All pairs of the device FP32 matrix X into R without any device
+    allocation (the standardized matrix lives in the library's fixed 32 MiB
+    device array); see include/pcc.h for the size limit."""
+    assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+    _check(load().pcc_allpairs_upper_noalloc(
+        _ptr(X), X.shape[0], X.shape[1], X.stride(0), _prec(prec), _ptr(R),
+        _ptr(d_status), _stream(stream)), "pcc_allpairs_upper_noalloc")
+    return R
 
 
 def pcc_sync_status(Z: Zmat, stream=None) -> int:
