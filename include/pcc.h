@@ -66,7 +66,8 @@ typedef enum {
                              s = floor(log2(l)/2); about 30x more accurate */
     PCC_PREC_BF16X1 = 4,  /* Z = bf16(z), one product (reported only:
                              about 1e-3 error) */
-    PCC_PREC_AUTO = 5     /* the tuner's choice among the split forms */
+    PCC_PREC_AUTO = 5     /* the more accurate split form for the row
+                             length: FP16X3S for l < 512, else BF16X3 */
 } pcc_prec;
 
 typedef struct pcc_zmat pcc_zmat; /* opaque, library-owned */
@@ -166,10 +167,17 @@ pcc_status pcc_perm_test(const pcc_zmat *Z, const int32_t *d_perms,
                          int32_t P, int32_t k0, int32_t k1,
                          uint32_t *d_counts, void *stream);
 
-/* All pairs of B independent matrices in one persistent launch: Rs[b] is
- * the packed FP32 triangle of Zs[b] (all Zs tensor-core forms on the same
- * device).  The first call with a given set allocates and caches a work
- * list. */
+/* All pairs of B independent matrices of uneven n and l in one persistent
+ * launch: Rs[b] (device, n_b(n_b-1)/2 floats) receives the packed FP32
+ * triangle of Zs[b].  All Zs are tensor-core forms on one device; each may
+ * use its own split form.  The work units of all matrices are spread over
+ * the CTAs longest first by a cost model (pcc_set_tuning).  The first call
+ * with a given set of (Zs, Rs) builds and caches a device work list (a small
+ * allocation); later calls with the same set allocate nothing, so make the
+ * first one before capturing a stream.  Device errors are reported in
+ * Zs[0]'s status word.
+ * Errors: PCC_ERR_INVALID_ARG for B < 1, NULL entries, a non tensor-core Z
+ * or Zs on different devices; PCC_ERR_OOM. */
 pcc_status pcc_allpairs_upper_batched(const pcc_zmat *const *Zs, int32_t B,
                                       float *const *Rs, void *stream);
 
@@ -201,6 +209,27 @@ pcc_status pcc_allpairs_upper_noalloc(const float *X, int64_t n, int64_t l,
 /* Synchronise `stream`, then return and clear the device status word of Z
  * (PCC_OK, PCC_ERR_TIMEOUT or PCC_ERR_CAPACITY). */
 pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
+
+/* Knobs of the tensor-core kernels, as chosen by the tuner
+ * (paper_1605_01584_gb300/autotune.py); they affect later launches only and
+ * never the result.  0 (or <= 0 for the costs) keeps a value.
+ *   stage_k    K per shared-memory ring stage: 32 (4 stages) or 64 (2).
+ *   cluster    2 = CTA pairs that share the column operand by TMA
+ *              multicast, 1 = independent CTAs.
+ *   band_rows  super-tile rows per band of the pair schedule (rows of a
+ *              band stay in L2 while column panels stream once per band).
+ *   cost_c0, cost_c1  cost model of pcc_allpairs_upper_batched's work
+ *              split: cycles per work unit outside the K loop and per K
+ *              block of 32 per product.
+ * Errors: PCC_ERR_INVALID_ARG for a value out of range (nothing changes).
+ * The paper has no counterpart (its tile size t is fixed at 4). */
+pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
+                          double cost_c0, double cost_c1);
+
+/* Current knob values (any pointer may be NULL). */
+pcc_status pcc_get_tuning(int32_t *stage_k, int32_t *cluster,
+                          int32_t *band_rows, double *cost_c0,
+                          double *cost_c1);
 
 /* Limit, in nanoseconds, of every pipeline wait inside the tensor-core
  * kernels (default 4e9).  A wait that runs out sets PCC_ERR_TIMEOUT in the

@@ -91,6 +91,9 @@ def load(path: str | None = None):
         "pcc_allpairs_upper_noalloc": (_ST, [_P, _I64, _I64, _I64, _I32, _P,
                                              _P, _P]),
         "pcc_set_wait_limit_ns": (_ST, [_U64]),
+        "pcc_set_tuning": (_ST, [_I32, _I32, _I32, ctypes.c_double,
+                                 ctypes.c_double]),
+        "pcc_get_tuning": (_ST, [_P, _P, _P, _P, _P]),
         "pcc_num_pairs": (_I64, [_I64]),
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
         "pcc_pair_coords": (_ST, [_I64, _I64, _P, _P]),
@@ -239,6 +242,23 @@ def pcc_sync_status(Z: Zmat, stream=None) -> int:
 
 def pcc_set_wait_limit_ns(ns: int):
     _check(load().pcc_set_wait_limit_ns(int(ns)), "pcc_set_wait_limit_ns")
+
+
+def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,
+                   cost_c1=0.0):
+    _check(load().pcc_set_tuning(int(stage_k), int(cluster), int(band_rows),
+                                 float(cost_c0), float(cost_c1)),
+           "pcc_set_tuning")
+
+
+def pcc_get_tuning() -> dict:
+    k, c, b = _I32(), _I32(), _I32()
+    c0, c1 = ctypes.c_double(), ctypes.c_double()
+    _check(load().pcc_get_tuning(ctypes.byref(k), ctypes.byref(c),
+                                 ctypes.byref(b), ctypes.byref(c0),
+                                 ctypes.byref(c1)), "pcc_get_tuning")
+    return dict(stage_k=k.value, cluster=c.value, band_rows=b.value,
+                cost_c0=c0.value, cost_c1=c1.value)
 
 
 def pcc_num_pairs(n: int) -> int:

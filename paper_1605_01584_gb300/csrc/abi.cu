@@ -49,10 +49,15 @@ bool device_is_sm103(int dev) {
   return maj == 10 && min == 3;
 }
 
-pcc_prec resolve_prec(pcc_prec p) {
-  // the tuner's default for the split forms: FP16 halves with a
-  // power-of-two row scale are as fast as BF16 halves and more accurate
-  return p == PCC_PREC_AUTO ? PCC_PREC_FP16X3S : p;
+pcc_prec resolve_prec(pcc_prec p, int64_t l) {
+  // Both split forms cost the same; their error has two parts: how well the
+  // two halves represent z (FP16 halves: ~2^-22, BF16: ~2^-17) and the
+  // tensor cores' FP32 accumulation, which rounds toward zero at every
+  // update and loses more with FP16 halves.  Measured max |dr| on |r| ~ 1:
+  //   l = 256: FP16 1.9e-6, BF16 3.8e-6;  l = 512: 3.3e-6 vs 2.8e-6;
+  //   l = 1024: 6.5e-6 vs 4.5e-6;  l = 2048: 1.3e-5 vs 8.4e-6.
+  if (p != PCC_PREC_AUTO) return p;
+  return l < 512 ? PCC_PREC_FP16X3S : PCC_PREC_BF16X3;
 }
 
 int32_t scale_exp_for(int64_t l) {
@@ -80,6 +85,33 @@ int num_sms(int device) {
 }
 
 uint64_t wait_limit_ns() { return g_wait_ns.load(); }
+
+namespace {
+std::mutex g_tune_mu;
+TcTuning g_tune = [] {
+  TcTuning t;
+  const char* e = getenv("PCC_TC_BK");
+  t.stage_k = (e && atoi(e) == 64) ? 64 : 32;
+  e = getenv("PCC_TC_CLUSTER");
+  t.cluster = (e && atoi(e) == 1) ? 1 : 2;
+  e = getenv("PCC_TC_BAND");
+  const int v = e ? atoi(e) : 0;
+  t.band = (v >= 1 && v <= 4096) ? v : 32;
+  t.cost_c0 = 3000.0;
+  t.cost_c1 = 260.0;
+  return t;
+}();
+}  // namespace
+
+TcTuning tc_tuning() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_tune;
+}
+
+void tc_set_tuning(const TcTuning& t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune = t;
+}
 
 cudaError_t ensure_func_smem(const void* func, int bytes) {
   return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -228,7 +260,7 @@ pcc_status pcc_standardize(const void* X, pcc_dtype xt, int64_t n, int64_t l,
     return PCC_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PCC_ERR_CUDA;
-  const pcc_prec rp = resolve_prec(prec);
+  const pcc_prec rp = resolve_prec(prec, l);
   if (is_split(rp) && !device_is_sm103(dev)) return PCC_ERR_UNSUPPORTED;
   if (!zmat_matches(*Z, dev, n, l, rp)) {
     pcc_zmat* nz = nullptr;
@@ -330,8 +362,46 @@ pcc_status pcc_perm_test(const pcc_zmat* Z, const int32_t* d_perms, int32_t P,
 
 pcc_status pcc_allpairs_upper_batched(const pcc_zmat* const* Zs, int32_t B,
                                       float* const* Rs, void* stream) {
-  (void)Zs; (void)B; (void)Rs; (void)stream;
-  return PCC_ERR_UNSUPPORTED;
+  if (!Zs || !Rs || B < 1 || B > (1 << 20)) return PCC_ERR_INVALID_ARG;
+  for (int32_t b = 0; b < B; ++b) {
+    if (!Zs[b] || !Rs[b] || !is_split(Zs[b]->prec) ||
+        Zs[b]->device != Zs[0]->device)
+      return PCC_ERR_INVALID_ARG;
+  }
+  return allpairs_batched(Zs, B, Rs, static_cast<cudaStream_t>(stream));
+}
+
+pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
+                          double cost_c0, double cost_c1) {
+  TcTuning t = tc_tuning();
+  if (stage_k) {
+    if (stage_k != 32 && stage_k != 64) return PCC_ERR_INVALID_ARG;
+    t.stage_k = stage_k;
+  }
+  if (cluster) {
+    if (cluster != 1 && cluster != 2) return PCC_ERR_INVALID_ARG;
+    t.cluster = cluster;
+  }
+  if (band_rows) {
+    if (band_rows < 1 || band_rows > 4096) return PCC_ERR_INVALID_ARG;
+    t.band = band_rows;
+  }
+  if (cost_c0 > 0) t.cost_c0 = cost_c0;
+  if (cost_c1 > 0) t.cost_c1 = cost_c1;
+  tc_set_tuning(t);
+  return PCC_OK;
+}
+
+pcc_status pcc_get_tuning(int32_t* stage_k, int32_t* cluster,
+                          int32_t* band_rows, double* cost_c0,
+                          double* cost_c1) {
+  const TcTuning t = tc_tuning();
+  if (stage_k) *stage_k = t.stage_k;
+  if (cluster) *cluster = t.cluster;
+  if (band_rows) *band_rows = (int32_t)t.band;
+  if (cost_c0) *cost_c0 = t.cost_c0;
+  if (cost_c1) *cost_c1 = t.cost_c1;
+  return PCC_OK;
 }
 
 pcc_status pcc_sync_status(pcc_zmat* Z, void* stream) {

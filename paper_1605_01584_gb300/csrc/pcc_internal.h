@@ -50,6 +50,19 @@ bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
                         int64_t rows, int64_t cols, int box_rows, int box_cols,
                         bool bf16);
 
+// Knobs of the tensor-core kernels (the tuner's choices).  Initial values
+// come from PCC_TC_BK, PCC_TC_CLUSTER, PCC_TC_BAND; pcc_set_tuning changes
+// them for later launches.
+struct TcTuning {
+  int stage_k;       // K per ring stage: 32 or 64
+  int cluster;       // 2 = CTA pairs sharing B by multicast, 1 = single CTAs
+  int64_t band;      // super-tile rows per band of the pair schedule
+  double cost_c0;    // batched plan: cycles per unit outside the K loop
+  double cost_c1;    // batched plan: cycles per K block and product
+};
+TcTuning tc_tuning();
+void tc_set_tuning(const TcTuning& t);
+
 // K1: standardize rows of X into Z's storage.
 cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
                                pcc_zmat* Z, cudaStream_t s);
@@ -69,6 +82,10 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
                             int64_t t1, bool edges_on, float tau,
                             pcc_edge* edges, uint64_t cap,
                             unsigned long long* count, cudaStream_t s);
+
+// K7: all pairs of B matrices in one persistent launch.
+pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
+                            float* const* Rs, cudaStream_t s);
 
 // K6: permutation test over permutations [k0, k1) of d_perms (P x l).
 pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,

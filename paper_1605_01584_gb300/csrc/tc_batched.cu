@@ -1,0 +1,486 @@
+// tc_batched.cu -- K7: all pairs of many matrices of uneven n and l in one
+// persistent tensor-core launch.
+//
+// Every matrix b keeps its own standardized halves, TMA maps, flags and
+// packed output; a device array of descriptors holds them.  The work units
+// of all matrices (128 x 256 halves of 256 x 256 super-tiles, banded order
+// of pcc_sched.h per matrix) are assigned to the CTAs on the host: units
+// are taken longest first and each goes to the CTA with the least estimated
+// work so far (cost = c0 + c1 * K-blocks * products), then each CTA's list
+// is put back in (matrix, unit) order so that CTAs walk the matrices
+// together.  The split form (3 products or 1, BF16 or FP16 halves) is read
+// per matrix at run time, so one kernel serves the whole batch.
+//
+// Same roles, pipeline and bounded waits as the single-matrix kernel
+// (tc_pairs.cu), single CTAs, K = 32 per stage; matrices with rows longer
+// than 1024 split their K blocks over two accumulators as that kernel does.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <queue>
+#include <vector>
+
+#include "pcc_internal.h"
+#include "pcc_ptx.cuh"
+#include "pcc_sched.h"
+#include "tc_epilogue.cuh"
+
+namespace pcc {
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kKB = 32, kUK = 16;
+constexpr int kThreads = 320, kEpiWarps = 8;
+constexpr int kTileA = kBM * kKB * 2;            // 8 KB
+constexpr int kTileB = kBN * kKB * 2;            // 16 KB
+constexpr int kStageBytes = 2 * (kTileA + kTileB);  // 48 KB (3 products)
+constexpr int kStages = 4;
+constexpr int kEpiBytes = kEpiWarps * 32 * kStagePad * 4;
+constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kEpiBytes + 256;
+static_assert(kSmemBytes <= 232448, "shared memory budget");
+
+struct alignas(64) MatDesc {
+  CUtensorMap tm_hi;  // box 32 x 128, 64-B swizzle
+  CUtensorMap tm_lo;
+  int64_t n;
+  int64_t m;          // super-tiles per side
+  int nkb;            // K blocks of 32
+  int nprod;          // 3 or 1
+  int kalt;           // even/odd K blocks in two accumulators (long rows)
+  uint32_t idesc;     // MMA instruction descriptor (BF16 or FP16 halves)
+  float scale;        // accumulator -> r
+  const uint8_t* flags;
+  float* R;
+};
+
+struct BatchParams {
+  const MatDesc* descs;
+  const uint64_t* items;   // (matrix << 40) | unit
+  const int64_t* cta_off;  // items of CTA c: [cta_off[c], cta_off[c+1])
+  int64_t G;               // band height
+  int* status;
+  uint64_t wait_ns;
+};
+
+constexpr int kItemShift = 40;
+constexpr uint64_t kItemMask = (1ull << kItemShift) - 1;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_pairs_tc_batched(const BatchParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* ring = smem;
+  float* epi = reinterpret_cast<float*>(smem + kStages * kStageBytes);
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + kEpiBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* tfull = bars + 2 * kStages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* mdone = tempty + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  auto sA_hi = [&](int s) { return ring + s * kStageBytes; };
+  auto sB_hi = [&](int s) { return ring + s * kStageBytes + kTileA; };
+  auto sA_lo = [&](int s) { return ring + s * kStageBytes + kTileA + kTileB; };
+  auto sB_lo = [&](int s) {
+    return ring + s * kStageBytes + 2 * kTileA + kTileB;
+  };
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kEpiWarps);
+    }
+    mbar_init(mdone, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_holder, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+  WaitCtx w{abort_flag, p.status, p.wait_ns};
+  const int64_t it0 = p.cta_off[blockIdx.x], it1 = p.cta_off[blockIdx.x + 1];
+
+  // unit coordinates; the band cursor restarts when the matrix changes
+  struct Walk {
+    int64_t b = -1;
+    BandCursor cur;
+  };
+  auto coords = [&](Walk& wk, uint64_t item, const MatDesc*& d,
+                    int64_t* row0, int64_t* col0) {
+    const int64_t b = (int64_t)(item >> kItemShift);
+    const int64_t u = (int64_t)(item & kItemMask);
+    d = p.descs + b;
+    if (b != wk.b) {
+      wk.b = b;
+      band_cursor_init(&wk.cur, d->m, p.G);
+    }
+    int64_t yt, xt;
+    band_tile_coords(&wk.cur, d->m, p.G, u >> 1, &yt, &xt);
+    *row0 = yt * kTcSuper + (u & 1) * kBM;
+    *col0 = xt * kTcSuper;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint64_t pol = l2_policy_evict_last();
+      Walk wk;
+      int stage = 0;
+      uint32_t phase = 0, issued_mask = 0, last_phase[kStages];
+      for (int s = 0; s < kStages; ++s) last_phase[s] = 0;
+      bool ok = true;
+      for (int64_t it = it0; it < it1 && ok; ++it) {
+        const MatDesc* d;
+        int64_t row0, col0;
+        coords(wk, p.items[it], d, &row0, &col0);
+        const int nkb = d->nkb, nprod = d->nprod;
+        const uint32_t bytes =
+            nprod == 3 ? (uint32_t)kStageBytes : (uint32_t)(kTileA + kTileB);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, w)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[stage], bytes);
+          const int kc = kb * kKB;
+          tma_load_2d_hint(sA_hi(stage), &d->tm_hi, &full[stage], kc,
+                           (int)row0, pol);
+          tma_load_2d_hint(sB_hi(stage), &d->tm_hi, &full[stage], kc,
+                           (int)col0, pol);
+          tma_load_2d_hint(sB_hi(stage) + kTileA, &d->tm_hi, &full[stage], kc,
+                           (int)col0 + kBM, pol);
+          if (nprod == 3) {
+            tma_load_2d_hint(sA_lo(stage), &d->tm_lo, &full[stage], kc,
+                             (int)row0, pol);
+            tma_load_2d_hint(sB_lo(stage), &d->tm_lo, &full[stage], kc,
+                             (int)col0, pol);
+            tma_load_2d_hint(sB_lo(stage) + kTileA, &d->tm_lo, &full[stage],
+                             kc, (int)col0 + kBM, pol);
+          }
+          issued_mask |= 1u << stage;
+          last_phase[stage] = phase;
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      WaitCtx wd = w;
+      volatile int never = 0;
+      wd.abort_flag = &never;
+      for (int s = 0; s < kStages; ++s)
+        if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      Walk wk;
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, aphase = 0;
+      bool ok = true;
+      for (int64_t it = it0; it < it1 && ok; ++it) {
+        const MatDesc* d;
+        int64_t row0, col0;
+        coords(wk, p.items[it], d, &row0, &col0);
+        const int nkb = d->nkb, nprod = d->nprod, kalt = d->kalt;
+        const uint32_t idesc = d->idesc;
+        if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
+        const int acc0 = acc;
+        if (kalt) {
+          acc ^= 1;
+          if (acc == 0) aphase ^= 1u;
+          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem0 = tmem_base + (uint32_t)(acc0 * kBN);
+        const uint32_t d_tmem1 = tmem_base + (uint32_t)(acc * kBN);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const uint32_t d_tmem = (kalt && (kb & 1)) ? d_tmem1 : d_tmem0;
+          const uint32_t first = kalt ? (kb < 2) : (kb == 0);
+          if (!mbar_wait(&full[stage], phase, w)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aH = smem_u32(sA_hi(stage));
+          const uint32_t bH = smem_u32(sB_hi(stage));
+          const uint32_t aL = smem_u32(sA_lo(stage));
+          const uint32_t bL = smem_u32(sB_lo(stage));
+#pragma unroll
+          for (int ks = 0; ks < kKB / kUK; ++ks) {
+            const uint32_t off = ks * kUK * 2;
+            const uint64_t dAH = kmajor_desc<64>(aH + off);
+            const uint64_t dBH = kmajor_desc<64>(bH + off);
+            umma_f16(d_tmem, dAH, dBH, idesc, (first && ks == 0) ? 0u : 1u);
+            if (nprod == 3) {
+              umma_f16(d_tmem, dAH, kmajor_desc<64>(bL + off), idesc, 1u);
+              umma_f16(d_tmem, kmajor_desc<64>(aL + off), dBH, idesc, 1u);
+            }
+          }
+          umma_commit(&empty[stage]);
+          if (++stage == kStages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(&tfull[acc0]);
+        if (kalt) umma_commit(&tfull[acc]);
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1u;
+      }
+      umma_commit(mdone);
+      WaitCtx wd = w;
+      volatile int never = 0;
+      wd.abort_flag = &never;
+      mbar_wait(mdone, 0, wd);
+    }
+  } else {
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    float* stg = epi + (warp - 2) * 32 * kStagePad;
+    Walk wk;
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int64_t it = it0; it < it1; ++it) {
+      const MatDesc* d;
+      int64_t row0, col0;
+      coords(wk, p.items[it], d, &row0, &col0);
+      const int64_t n = d->n;
+      const int64_t rbase = row0 + q * 32;
+      const int64_t jw0 = col0 + h * 128;
+      const int64_t my_i = rbase + lane;
+      const int rf = (my_i < n) ? d->flags[my_i] : 1;
+      int cfl[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int64_t jj = jw0 + c * 32 + lane;
+        cfl[c] = (jj < n) ? d->flags[jj] : 1;
+      }
+      const EpiOut eo{d->R, d->scale, 2.f, nullptr, nullptr, 0, p.status};
+      const int kalt = d->kalt;
+      bool okw = true;
+      const int acc0 = acc;
+      if (lane == 0) okw = mbar_wait(&tfull[acc], aphase, w);
+      if (kalt) {
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1u;
+        if (lane == 0 && okw) okw = mbar_wait(&tfull[acc], aphase, w);
+      }
+      if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) break;
+      tc_fence_after();
+      const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
+      const int64_t base0 = pair_row_base(n, rbase);
+      const uint32_t lane_off =
+          ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
+      const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
+      if (kalt)
+        epilogue_rows<true, false, true>(
+            t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo,
+            tmem_base + lane_off + (uint32_t)(acc * kBN));
+      else
+        epilogue_rows<true, false>(t_row, stg, lane, n, rbase, jw0, base0,
+                                   rflags, cfl, eo);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&tempty[acc0]);
+        if (kalt) mbar_arrive(&tempty[acc]);
+      }
+      acc ^= 1;
+      if (acc == 0) aphase ^= 1u;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    tmem_dealloc(tmem_base, 512);
+  }
+}
+
+// ------------------------------------------------------------- host plan
+struct Plan {
+  std::vector<const pcc_zmat*> zs;
+  std::vector<float*> rs;
+  std::vector<int64_t> sig;  // n, lpad, prec, hi address per matrix
+  TcTuning tuning;
+  int device = -1;
+  int grid = 0;
+  void* dmem = nullptr;  // descs | cta_off | items
+  MatDesc* d_descs = nullptr;
+  int64_t* d_off = nullptr;
+  uint64_t* d_items = nullptr;
+};
+
+std::mutex g_plan_mu;
+std::vector<Plan*> g_plans;  // small cache, most recent last
+
+bool build_plan(Plan* P) {
+  const int B = (int)P->zs.size();
+  const int sms = num_sms(P->device);
+  const TcTuning tn = tc_tuning();
+  std::vector<MatDesc> descs(B);
+  struct U {
+    double cost;
+    uint64_t item;
+  };
+  std::vector<U> units;
+  for (int b = 0; b < B; ++b) {
+    const pcc_zmat* Z = P->zs[b];
+    MatDesc& d = descs[b];
+    memset(&d, 0, sizeof(d));
+    d.tm_hi = Z->tm_hi32;
+    d.tm_lo = Z->tm_lo32;
+    d.n = Z->n;
+    d.m = tc_super_count(Z->n);
+    d.nkb = (int)(Z->lpad / kKB);
+    d.nprod = Z->prec == PCC_PREC_BF16X1 ? 1 : 3;
+    d.kalt = (Z->lpad > 1024 && d.nkb >= 2) ? 1 : 0;
+    d.idesc = make_idesc_f16(Z->prec != PCC_PREC_FP16X3S, kBM, kBN);
+    d.scale = (float)ldexp(1.0, -2 * Z->scale_exp);
+    d.flags = Z->flags;
+    d.R = P->rs[b];
+    const int64_t nu = 2 * tc_num_tiles(Z->n);
+    const double cost = tn.cost_c0 + tn.cost_c1 * d.nkb * d.nprod;
+    BandCursor cur;
+    band_cursor_init(&cur, d.m, tc_tuning().band);
+    for (int64_t u = 0; u < nu; ++u) {
+      int64_t yt, xt;
+      band_tile_coords(&cur, d.m, tc_tuning().band, u >> 1, &yt, &xt);
+      if (yt * kTcSuper + (u & 1) * kBM >= Z->n) continue;  // empty half
+      units.push_back({cost, ((uint64_t)b << kItemShift) | (uint64_t)u});
+    }
+  }
+  const int64_t total = (int64_t)units.size();
+  int grid = (int)std::min<int64_t>(sms, std::max<int64_t>(total, 1));
+  // longest first, each to the least-loaded CTA
+  std::stable_sort(units.begin(), units.end(),
+                   [](const U& a, const U& b) { return a.cost > b.cost; });
+  typedef std::pair<double, int> L;
+  std::priority_queue<L, std::vector<L>, std::greater<L>> heap;
+  for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+  std::vector<std::vector<uint64_t>> per(grid);
+  for (const U& u : units) {
+    L top = heap.top();
+    heap.pop();
+    per[top.second].push_back(u.item);
+    heap.push({top.first + u.cost, top.second});
+  }
+  std::vector<int64_t> off(grid + 1, 0);
+  std::vector<uint64_t> items;
+  items.reserve(total);
+  for (int c = 0; c < grid; ++c) {
+    std::sort(per[c].begin(), per[c].end());
+    off[c] = (int64_t)items.size();
+    items.insert(items.end(), per[c].begin(), per[c].end());
+  }
+  off[grid] = (int64_t)items.size();
+  const size_t bd = sizeof(MatDesc) * B;
+  const size_t bo = sizeof(int64_t) * (grid + 1);
+  const size_t bi = sizeof(uint64_t) * std::max<size_t>(items.size(), 1);
+  const size_t o_off = (bd + 255) / 256 * 256;
+  const size_t o_items = o_off + (bo + 255) / 256 * 256;
+  if (cudaMalloc(&P->dmem, o_items + bi) != cudaSuccess) {
+    cudaGetLastError();
+    P->dmem = nullptr;
+    return false;
+  }
+  uint8_t* base = static_cast<uint8_t*>(P->dmem);
+  P->d_descs = reinterpret_cast<MatDesc*>(base);
+  P->d_off = reinterpret_cast<int64_t*>(base + o_off);
+  P->d_items = reinterpret_cast<uint64_t*>(base + o_items);
+  if (cudaMemcpy(P->d_descs, descs.data(), bd, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(P->d_off, off.data(), bo, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      (!items.empty() &&
+       cudaMemcpy(P->d_items, items.data(), sizeof(uint64_t) * items.size(),
+                  cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaFree(P->dmem);
+    P->dmem = nullptr;
+    return false;
+  }
+  P->grid = grid;
+  return true;
+}
+
+}  // namespace
+
+pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
+                            float* const* Rs, cudaStream_t s) {
+  int dev = Zs[0]->device;
+  Plan* P = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (Plan* q : g_plans) {
+      if ((int)q->zs.size() != B || q->device != dev) continue;
+      bool same = q->tuning.band == tc_tuning().band &&
+                  q->tuning.cost_c0 == tc_tuning().cost_c0 &&
+                  q->tuning.cost_c1 == tc_tuning().cost_c1;
+      for (int b = 0; b < B && same; ++b)
+        same = q->zs[b] == Zs[b] && q->rs[b] == Rs[b] &&
+               q->sig[4 * b] == Zs[b]->n && q->sig[4 * b + 1] == Zs[b]->lpad &&
+               q->sig[4 * b + 2] == (int64_t)Zs[b]->prec &&
+               q->sig[4 * b + 3] == (int64_t)(uintptr_t)Zs[b]->hi;
+      if (same) {
+        P = q;
+        break;
+      }
+    }
+    if (!P) {
+      P = new Plan();
+      P->zs.assign(Zs, Zs + B);
+      P->rs.assign(Rs, Rs + B);
+      for (int b = 0; b < B; ++b) {
+        P->sig.push_back(Zs[b]->n);
+        P->sig.push_back(Zs[b]->lpad);
+        P->sig.push_back((int64_t)Zs[b]->prec);
+        P->sig.push_back((int64_t)(uintptr_t)Zs[b]->hi);
+      }
+      P->tuning = tc_tuning();
+      P->device = dev;
+      if (!build_plan(P)) {
+        delete P;
+        return PCC_ERR_OOM;
+      }
+      g_plans.push_back(P);
+      if (g_plans.size() > 8) {
+        Plan* old = g_plans.front();
+        cudaDeviceSynchronize();  // its last launch may be on any stream
+        cudaFree(old->dmem);
+        delete old;
+        g_plans.erase(g_plans.begin());
+      }
+    }
+  }
+  cudaError_t e = ensure_func_smem(
+      reinterpret_cast<const void*>(k_pairs_tc_batched), kSmemBytes);
+  if (e != cudaSuccess) return cuda_status(e);
+  BatchParams bp;
+  bp.descs = P->d_descs;
+  bp.items = P->d_items;
+  bp.cta_off = P->d_off;
+  bp.G = tc_tuning().band;
+  bp.status = Zs[0]->status;
+  bp.wait_ns = wait_limit_ns();
+  k_pairs_tc_batched<<<P->grid, kThreads, kSmemBytes, s>>>(bp);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace pcc

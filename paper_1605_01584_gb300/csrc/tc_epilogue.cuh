@@ -1,0 +1,158 @@
+// tc_epilogue.cuh -- the store side shared by the tensor-core pair kernels:
+// one warp turns 32 rows x 128 columns of a TMEM accumulator into packed
+// upper-triangle values (and optional |r| >= tau edges).
+//
+// Row i's pairs are contiguous in the packed layout, J(i,j) = base(i) + j,
+// base(i+1) = base(i) + n - i - 2.  TMEM hands thread t the columns of row
+// t, so each 32 x 32 block goes through a shared-memory transpose; the warp
+// then stores 32 consecutive pairs of one row per instruction.  Blocks with
+// no pair i < j < n are skipped, blocks that are entirely valid and
+// unflagged take a branch-free path, and the (rare) edge append rescans a
+// block only when some |r| >= tau.
+//
+// Why two accumulators for long rows: the tensor cores' FP32 accumulation
+// rounds every update toward zero, so its error grows with the number of
+// updates into a large partial sum (measured: 1.2e-5 on |r| ~ 1 at l = 2048
+// with one accumulator, always toward smaller |r|).  Alternating K blocks
+// between two accumulators halves both the updates and the partial sum of
+// each, and their sum is formed here with round-to-nearest.
+#pragma once
+#include <stdint.h>
+
+#include "pcc.h"
+#include "pcc_ptx.cuh"
+
+namespace pcc {
+
+constexpr int kStagePad = 33;  // transpose row pitch (conflict-free)
+
+struct EpiOut {
+  float* R;                    // packed output (or null)
+  float scale;                 // accumulator -> r (2^-2s for FP16X3S)
+  float tau;                   // edge threshold
+  pcc_edge* edges;
+  unsigned long long* count;
+  uint64_t cap;
+  int* status;
+};
+
+// t_row: TMEM address of (lane 32q, first column of the warp's 128); with
+// DUAL the accumulator is split over two TMEM buffers (even and odd K
+// blocks) and t_row2 addresses the second, summed here in FP32; stg: this
+// warp's 32 x kStagePad floats; rbase: first row; jw0: first column; base0 =
+// pair_row_base(n, rbase); rflags: bit rr = row rbase+rr flagged (or >= n);
+// cfl[c]: flag of column jw0 + 32c + lane.
+template <bool WRITE_R, bool EDGES, bool DUAL = false>
+__device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
+                                              int lane, int64_t n,
+                                              int64_t rbase, int64_t jw0,
+                                              int64_t base0, uint32_t rflags,
+                                              const int (&cfl)[4],
+                                              const EpiOut& eo,
+                                              uint32_t t_row2 = 0) {
+  // warp-uniform: does 32 x 32 block c hold any pair i < j < n?
+  auto active = [&](int c) {
+    const int64_t jc0 = jw0 + c * 32;
+    return !(rbase >= n || jc0 >= n || jc0 + 31 <= rbase);
+  };
+  auto next_active = [&](int c) {
+    ++c;
+    while (c < 4 && !active(c)) ++c;
+    return c;
+  };
+  uint32_t v[32];
+  uint32_t v2[DUAL ? 32 : 1];
+  int c = next_active(-1);
+  if (c < 4) {
+    tmem_ld_32x32b_x32(t_row + (uint32_t)(c * 32), v);
+    if constexpr (DUAL) tmem_ld_32x32b_x32(t_row2 + (uint32_t)(c * 32), v2);
+  }
+  while (c < 4) {
+    tmem_ld_wait();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      float a = __uint_as_float(v[t]);
+      if constexpr (DUAL) a += __uint_as_float(v2[t]);
+      stg[lane * kStagePad + t] = a;
+    }
+    __syncwarp();
+    // the next block's TMEM load overlaps this block's stores
+    const int cn = next_active(c);
+    if (cn < 4) {
+      tmem_ld_32x32b_x32(t_row + (uint32_t)(cn * 32), v);
+      if constexpr (DUAL)
+        tmem_ld_32x32b_x32(t_row2 + (uint32_t)(cn * 32), v2);
+    }
+    const int64_t jc0 = jw0 + c * 32;
+    const int64_t j = jc0 + lane;
+    const bool cflag = cfl[c] != 0;
+    const bool clean = (jc0 > rbase + 31) && (jc0 + 31 < n) &&
+                       (rbase + 31 < n) && rflags == 0 &&
+                       !__any_sync(0xffffffffu, cflag);
+    float* out = eo.R + base0 + j;
+    int64_t step = n - rbase - 2;
+    bool hit = false;
+    if (clean) {
+      // every pair of the block is valid and unflagged
+#pragma unroll 8
+      for (int rr = 0; rr < 32; ++rr) {
+        float r = stg[rr * kStagePad + lane] * eo.scale;
+        r = fminf(1.f, fmaxf(-1.f, r));
+        if constexpr (WRITE_R) __stcs(out, r);
+        if constexpr (EDGES) hit |= fabsf(r) >= eo.tau;
+        out += step;
+        --step;
+      }
+    } else {
+      hit = true;  // edges (if any) are handled by the scan below
+      if constexpr (WRITE_R) {
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+          const int64_t i = rbase + rr;
+          float r = stg[rr * kStagePad + lane] * eo.scale;
+          r = fminf(1.f, fmaxf(-1.f, r));
+          if (((rflags >> rr) & 1u) || cflag) r = __int_as_float(0x7fc00000);
+          if (i < n && j < n && j > i) __stcs(out, r);
+          out += step;
+          --step;
+        }
+      }
+    }
+    if constexpr (EDGES) {
+      if (__any_sync(0xffffffffu, hit)) {
+        // rare: rescan the block and append its edges, one atomic per warp
+        // and row
+        for (int rr = 0; rr < 32; ++rr) {
+          const int64_t i = rbase + rr;
+          float r = stg[rr * kStagePad + lane] * eo.scale;
+          r = fminf(1.f, fmaxf(-1.f, r));
+          const bool fl = ((rflags >> rr) & 1u) || cflag;
+          const bool e = i < n && j < n && j > i && !fl && fabsf(r) >= eo.tau;
+          const unsigned mask = __ballot_sync(0xffffffffu, e);
+          if (mask) {
+            const int leader = __ffs(mask) - 1;
+            unsigned long long b0 = 0;
+            if (lane == leader)
+              b0 = atomicAdd(eo.count, (unsigned long long)__popc(mask));
+            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            if (e) {
+              const unsigned long long idx =
+                  b0 + __popc(mask & ((1u << lane) - 1u));
+              if (idx < eo.cap) {
+                eo.edges[idx].i = (uint32_t)i;
+                eo.edges[idx].j = (uint32_t)j;
+                eo.edges[idx].r = r;
+              } else {
+                atomicCAS(eo.status, 0, (int)PCC_ERR_CAPACITY);
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+    c = cn;
+  }
+}
+
+}  // namespace pcc

@@ -44,6 +44,7 @@
 #include "pcc_internal.h"
 #include "pcc_ptx.cuh"
 #include "pcc_sched.h"
+#include "tc_epilogue.cuh"
 
 namespace pcc {
 namespace {
@@ -51,9 +52,9 @@ namespace {
 constexpr int kBM = 128;   // rows per unit (MMA M)
 constexpr int kBN = 256;   // columns per unit (MMA N)
 constexpr int kUK = 16;    // K per tcgen05.mma kind::f16
+constexpr int kKaltMinL = 1024;  // longer rows use two accumulators
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
-constexpr int kStagePad = 33;          // epilogue transpose row pitch
 
 struct TcParams {
   int64_t n;
@@ -62,6 +63,8 @@ struct TcParams {
   int64_t u_begin;   // units [u_begin, u_end)
   int64_t u_end;
   int nkb;           // K blocks of KB
+  int kalt;          // 1: even/odd K blocks go to two accumulators (both
+                     // TMEM buffers) for long rows
   float out_scale;   // 2^-2s for FP16X3S, else 1
   float tau;
   const uint8_t* flags;
@@ -254,10 +257,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         unit_coords(&cur, p, u, &row0, &col0);
         if (CL == 1 && row0 >= n) continue;
         if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
+        const int acc0 = acc;
+        if (p.kalt) {
+          // a long-row unit also takes the other buffer of the ring
+          acc ^= 1;
+          if (acc == 0) aphase ^= 1u;
+          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
+        }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kBN);
+        const uint32_t d_tmem0 = tmem_base + (uint32_t)(acc0 * kBN);
+        const uint32_t d_tmem1 = tmem_base + (uint32_t)(acc * kBN);
         bool ok = true;
         for (int kb = 0; kb < p.nkb; ++kb) {
+          const uint32_t d_tmem = (p.kalt && (kb & 1)) ? d_tmem1 : d_tmem0;
+          const uint32_t first = p.kalt ? (kb < 2) : (kb == 0);
           if (!mbar_wait(&full[stage], phase, w)) {
             ok = false;
             break;
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t off = ks * kUK * 2;  // bytes along K
             const uint64_t dAH = kmajor_desc<C::kSwz>(aH + off);
             const uint64_t dBH = kmajor_desc<C::kSwz>(bH + off);
-            umma_f16(d_tmem, dAH, dBH, kIdesc, (kb | ks) != 0);
+            umma_f16(d_tmem, dAH, dBH, kIdesc, (first && ks == 0) ? 0u : 1u);
             if (NPROD == 3) {
               const uint64_t dAL = kmajor_desc<C::kSwz>(aL + off);
               const uint64_t dBL = kmajor_desc<C::kSwz>(bL + off);
@@ -290,7 +303,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!ok) break;
-        umma_commit(&tfull[acc]);
+        umma_commit(&tfull[acc0]);
+        if (p.kalt) umma_commit(&tfull[acc]);
         acc ^= 1;
         if (acc == 0) aphase ^= 1u;
       }
@@ -328,111 +342,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         cfl[c] = (jj < n) ? p.flags[jj] : 1;
       }
       bool ok = true;
+      const int acc0 = acc;
       if (lane == 0) ok = mbar_wait(&tfull[acc], aphase, w);
+      if (p.kalt) {
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1u;
+        if (lane == 0 && ok) ok = mbar_wait(&tfull[acc], aphase, w);
+      }
       if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
       tc_fence_after();
       const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
       // packed index of (rbase, 0); row i+1 starts n - i - 2 later
       const int64_t base0 = pair_row_base(n, rbase);
-      const uint32_t t_row = tmem_base + ((uint32_t)(q * 32) << 16) +
-                             (uint32_t)(acc * kBN + h * 128);
-      // warp-uniform: does 32 x 32 block c hold any pair i < j < n?
-      auto active = [&](int c) {
-        const int64_t jc0 = jw0 + c * 32;
-        return !(rbase >= n || jc0 >= n || jc0 + 31 <= rbase);
-      };
-      auto next_active = [&](int c) {
-        ++c;
-        while (c < 4 && !active(c)) ++c;
-        return c;
-      };
-      uint32_t v[32];
-      int c = next_active(-1);
-      if (c < 4) tmem_ld_32x32b_x32(t_row + (uint32_t)(c * 32), v);
-      while (c < 4) {
-        tmem_ld_wait();
-#pragma unroll
-        for (int t = 0; t < 32; ++t)
-          stg[lane * kStagePad + t] = __uint_as_float(v[t]);
-        __syncwarp();
-        // the next block's TMEM load overlaps this block's stores
-        const int cn = next_active(c);
-        if (cn < 4) tmem_ld_32x32b_x32(t_row + (uint32_t)(cn * 32), v);
-        const int64_t jc0 = jw0 + c * 32;
-        const int64_t j = jc0 + lane;
-        const bool cflag = cfl[c] != 0;
-        const bool clean = (jc0 > rbase + 31) && (jc0 + 31 < n) &&
-                           (rbase + 31 < n) && rflags == 0 &&
-                           !__any_sync(0xffffffffu, cflag);
-        float* out = p.R + base0 + j;
-        int64_t step = n - rbase - 2;
-        bool hit = false;
-        if (clean) {
-          // every pair of the block is valid and unflagged
-#pragma unroll 8
-          for (int rr = 0; rr < 32; ++rr) {
-            float r = stg[rr * kStagePad + lane] * p.out_scale;
-            r = fminf(1.f, fmaxf(-1.f, r));
-            if constexpr (WRITE_R) __stcs(out, r);
-            if constexpr (EDGES) hit |= fabsf(r) >= p.tau;
-            out += step;
-            --step;
-          }
-        } else {
-          hit = true;  // edges (if any) are handled by the scan below
-          if constexpr (WRITE_R) {
-#pragma unroll 4
-            for (int rr = 0; rr < 32; ++rr) {
-              const int64_t i = rbase + rr;
-              float r = stg[rr * kStagePad + lane] * p.out_scale;
-              r = fminf(1.f, fmaxf(-1.f, r));
-              if (((rflags >> rr) & 1u) || cflag)
-                r = __int_as_float(0x7fc00000);
-              if (i < n && j < n && j > i) __stcs(out, r);
-              out += step;
-              --step;
-            }
-          }
-        }
-        if constexpr (EDGES) {
-          if (__any_sync(0xffffffffu, hit)) {
-            // rare: rescan the block and append its edges, one atomic per
-            // warp and row
-            for (int rr = 0; rr < 32; ++rr) {
-              const int64_t i = rbase + rr;
-              float r = stg[rr * kStagePad + lane] * p.out_scale;
-              r = fminf(1.f, fmaxf(-1.f, r));
-              const bool fl = ((rflags >> rr) & 1u) || cflag;
-              const bool e =
-                  i < n && j < n && j > i && !fl && fabsf(r) >= p.tau;
-              const unsigned mask = __ballot_sync(0xffffffffu, e);
-              if (mask) {
-                const int leader = __ffs(mask) - 1;
-                unsigned long long b0 = 0;
-                if (lane == leader)
-                  b0 = atomicAdd(p.count, (unsigned long long)__popc(mask));
-                b0 = __shfl_sync(0xffffffffu, b0, leader);
-                if (e) {
-                  const unsigned long long idx =
-                      b0 + __popc(mask & ((1u << lane) - 1u));
-                  if (idx < p.cap) {
-                    p.edges[idx].i = (uint32_t)i;
-                    p.edges[idx].j = (uint32_t)j;
-                    p.edges[idx].r = r;
-                  } else {
-                    atomicCAS(p.status, 0, (int)PCC_ERR_CAPACITY);
-                  }
-                }
-              }
-            }
-          }
-        }
-        __syncwarp();
-        c = cn;
-      }
+      const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
+      const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
+      const EpiOut eo{p.R, p.out_scale, p.tau, p.edges, p.count, p.cap,
+                      p.status};
+      if (p.kalt)
+        epilogue_rows<WRITE_R, EDGES, true>(
+            t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo,
+            tmem_base + lane_off + (uint32_t)(acc * kBN));
+      else
+        epilogue_rows<WRITE_R, EDGES>(t_row, stg, lane, n, rbase, jw0, base0,
+                                      rflags, cfl, eo);
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[acc]);
+      if (lane == 0) {
+        mbar_arrive(&tempty[acc0]);
+        if (p.kalt) mbar_arrive(&tempty[acc]);
+      }
       acc ^= 1;
       if (acc == 0) aphase ^= 1u;
     }
@@ -449,28 +387,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Super-tile rows per band of the schedule: a band's row panels stay in L2
-// while each column panel is streamed once per band, so taller bands read
-// Z from DRAM fewer times (PCC_TC_BAND overrides the default).
-int64_t tc_band_rows() {
-  static int64_t g = [] {
-    const char* e = getenv("PCC_TC_BAND");
-    const int v = e ? atoi(e) : 0;
-    return (int64_t)(v >= 1 && v <= 1024 ? v : 32);
-  }();
-  return g;
-}
-
-// Pairs of CTAs (2-CTA clusters) share the B operand through TMA
-// multicast; PCC_TC_CLUSTER=1 selects single CTAs.
-bool tc_use_cluster() {
-  static bool on = [] {
-    const char* e = getenv("PCC_TC_CLUSTER");
-    return !(e && atoi(e) == 1);
-  }();
-  return on;
-}
-
 template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB>
 cudaError_t launch_inst(const pcc_zmat* Z, const TcParams& p, int grid,
                         cudaStream_t s) {
@@ -478,7 +394,7 @@ cudaError_t launch_inst(const pcc_zmat* Z, const TcParams& p, int grid,
   const CUtensorMap& th = KB == 64 ? Z->tm_hi : Z->tm_hi32;
   const CUtensorMap& tl = KB == 64 ? Z->tm_lo : Z->tm_lo32;
   const int64_t tiles = (p.u_end - p.u_begin) / 2;
-  if (tc_use_cluster() && tiles >= 2) {
+  if (tc_tuning().cluster == 2 && tiles >= 2) {
     auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2>;
     cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
@@ -530,6 +446,7 @@ template <int KB>
 cudaError_t launch_kb(const pcc_zmat* Z, TcParams& p, int grid, bool write_r,
                       bool edges_on, cudaStream_t s) {
   p.nkb = (int)(Z->lpad / KB);
+  p.kalt = (Z->lpad > kKaltMinL && p.nkb >= 2) ? 1 : 0;
   switch (Z->prec) {
     case PCC_PREC_BF16X3:
       return launch_prec<3, true, KB>(Z, p, grid, write_r, edges_on, s);
@@ -540,16 +457,6 @@ cudaError_t launch_kb(const pcc_zmat* Z, TcParams& p, int grid, bool write_r,
     default:
       return cudaErrorInvalidValue;
   }
-}
-
-// K per ring stage: PCC_TC_BK=64 or 32 (default 32) selects the pipeline
-// depth; both compute the same result.
-int tc_stage_k() {
-  static int kb = [] {
-    const char* e = getenv("PCC_TC_BK");
-    return (e && atoi(e) == 64) ? 64 : 32;
-  }();
-  return kb;
 }
 
 }  // namespace
@@ -567,7 +474,7 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
   TcParams p;
   p.n = Z->n;
   p.m = tc_super_count(Z->n);
-  p.G = tc_band_rows();
+  p.G = tc_tuning().band;
   p.u_begin = 2 * t0;
   p.u_end = 2 * t1;
   p.out_scale = (float)ldexp(1.0, -2 * Z->scale_exp);
@@ -583,7 +490,7 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
   int grid = num_sms(Z->device);
   if (units < grid) grid = (int)units;
   const bool write_r = R != nullptr;
-  if (tc_stage_k() == 64)
+  if (tc_tuning().stage_k == 64)
     return launch_kb<64>(Z, p, grid, write_r, edges_on, s);
   return launch_kb<32>(Z, p, grid, write_r, edges_on, s);
 }
