@@ -295,12 +295,12 @@ def run_gpu(args):
     # roofline of the dominant kernel (the fused pair kernel)
     hbm, bf16, bf16_sus, peak_kind = peaks()
     info = Z.info()
-    z_bytes = n * info["lpad"] * 2 * (1 if args.prec == "bf16x1" else 2)
+    z_bytes = n * info["lpad"] * 2 * (1 if info["prec"] == 4 else 2)
     alg_bytes = npairs * 4 + z_bytes + n + min(edges_found, EDGE_CAP) * 12
     pair_avg = statistics.mean(pair_ms)
     achieved_gbs = alg_bytes / (pair_avg / 1e3) / 1e9
     alg_flops = 2.0 * npairs * l
-    nprod = 1 if args.prec == "bf16x1" else 3
+    nprod = 1 if info["prec"] == 4 else 3
     exec_flops = nprod * 2.0 * (info["lpad"]) * 128 * 256 * 2 * (
         (-(-n // 256)) * (-(-n // 256) + 1) // 2)
     exec_tflops = exec_flops / (pair_avg / 1e3) / 1e12
@@ -310,11 +310,12 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16x3": "bf16", "fp16x3s": "f16",
-                  "bf16x1": "bf16"}.get(args.prec, args.prec),
+        "dtype": {2: "bf16", 3: "f16", 4: "bf16"}.get(info["prec"], "?"),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "l": l, "tau": TAU,
-                   "split": args.prec, "seed": SEED,
+                   "split": {2: "bf16x3", 3: "fp16x3s",
+                             4: "bf16x1"}.get(info["prec"], args.prec),
+                   "seed": SEED,
                    "per_rank": "independent matrix per GPU (seed + 1000*rank)",
                    "l2": "inputs larger than L2 (134 MB X; 8.6 GB output "
                          "streamed per step)"},
@@ -406,14 +407,121 @@ def run_gpu(args):
     return 0
 
 
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_perm(args):
+    """Permutation test workload: n=4096 x l=256, P=1000 seeded Fisher-Yates
+    permutations, counts of |r_k| >= |r_obs| for every pair."""
+    import torch
+    import paper_1605_01584_gb300 as pcc
+    import synth
+    pcc.load()
+    n, l, P = 4096, 256, 1000
+    X = synth.counts_log(n, l, 4)
+    perms = synth.fisher_yates_perms(P, l, seed=4)
+    Xd = torch.from_numpy(X).cuda()
+    dp = torch.from_numpy(perms).cuda()
+    Z = pcc.pcc_standardize(Xd, args.prec)
+    cnt = torch.zeros(n * (n - 1) // 2, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pcc.pcc_standardize(Xd, args.prec, Z=Z)
+        cnt.zero_()
+        pcc.pcc_perm_test(Z, dp, P, 0, P, cnt)
+
+    ms = _timed(step, max(3, min(args.steps, 20)), args.warmup, stream)
+    st = pcc.pcc_sync_status(Z)
+    info = Z.info()
+    tiles = (-(-n // 128)) * (-(-n // 128) + 1) // 2
+    exec_flops = 3 * 2 * 128 * 128 * info["lpad"] * tiles * (P + 1)
+    _, bf16, bf16_sus, kind = peaks()
+    out = {"metric": "permutation-test Gpair*samples*perms/s",
+           "value": n * (n - 1) / 2 * l * P / (ms / 1e3) / 1e9,
+           "unit": "Gpair*samples*perms/s", "ms_per_step": ms,
+           "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
+           "status": st, "dtype": {2: "bf16", 3: "f16"}.get(info["prec"]),
+           "config": {"workload": "permutation test n=4096 x l=256, P=1000",
+                      "split": args.prec},
+           "roofline_split_executed": {
+               "bound": "tensor", "achieved": exec_flops / (ms / 1e3) / 1e12,
+               "peak": bf16_sus, "unit": "TFLOP/s",
+               "frac": exec_flops / (ms / 1e3) / 1e12 / bf16_sus}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_batched(args):
+    """Batched uneven workload: 64 matrices, n ~ U{500..20000}, l ~
+    U{32..2048}, all pairs of each in one persistent launch."""
+    import torch
+    import paper_1605_01584_gb300 as pcc
+    import synth
+    pcc.load()
+    shapes = synth.uneven_shapes()
+    Xs, Zs, Rs = [], [], []
+    t0 = time.time()
+    for b, (n, l) in enumerate(shapes):
+        X = synth.counts_log(n, l, 5 * 1000 + b)
+        Xd = torch.from_numpy(X).cuda()
+        Xs.append(Xd)
+        Zs.append(pcc.pcc_standardize(Xd, args.prec))
+        Rs.append(torch.empty(n * (n - 1) // 2, device="cuda"))
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for Xd, Z in zip(Xs, Zs):
+            pcc.pcc_standardize(Xd, args.prec, Z=Z)
+        pcc.pcc_allpairs_upper_batched(Zs, Rs)
+
+    ms = _timed(step, max(3, min(args.steps, 10)), args.warmup, stream)
+
+    def kern():
+        pcc.pcc_allpairs_upper_batched(Zs, Rs)
+
+    ms_k = _timed(kern, max(3, min(args.steps, 10)), 1, stream)
+    st = pcc.pcc_sync_status(Zs[0])
+    work = sum(n * (n - 1) / 2 * l for n, l in shapes) / 1e9
+    out_bytes = sum(n * (n - 1) / 2 * 4 for n, l in shapes)
+    hbm, _, _, kind = peaks()
+    out = {"metric": "batched all-pairs Gpair*samples/s", "value": work /
+           (ms / 1e3), "unit": "Gpair*samples/s", "ms_per_step": ms,
+           "ms_batched_kernel": ms_k, "status": st,
+           "config": {"workload": "64 uneven matrices n~U{500..20000}, "
+                      "l~U{32..2048}", "split": args.prec,
+                      "matrices": len(shapes), "gen_seconds": gen_s},
+           "roofline": {"bound": "hbm", "achieved": out_bytes / (ms_k / 1e3)
+                        / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": out_bytes / (ms_k / 1e3) / 1e9 / hbm,
+                        "note": "output bytes only"}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--prec", default="fp16x3s",
-                    choices=["bf16x3", "fp16x3s", "bf16x1"])
+    ap.add_argument("--prec", default="auto",
+                    choices=["auto", "bf16x3", "fp16x3s", "bf16x1"])
+    ap.add_argument("--workload", default="allpairs",
+                    choices=["allpairs", "perm", "batched"])
     ap.add_argument("--n", type=int, default=N_GENES)
     ap.add_argument("--l", type=int, default=L_SAMPLES)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -425,6 +533,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "perm":
+        return run_perm(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 

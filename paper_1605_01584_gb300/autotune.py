@@ -1,0 +1,179 @@
+"""Tuner for the tensor-core kernels' knobs (pcc_set_tuning).
+
+The knobs never change results, only speed:
+  stage_k    K per shared-memory ring stage (32: 4 stages, 64: 2 stages)
+  cluster    2 = CTA pairs sharing the column operand by TMA multicast,
+             1 = independent CTAs
+  band_rows  super-tile rows per band of the pair schedule
+and the batched work split's cost model (cycles per unit c0, per K block and
+product c1).
+
+``tune_pairs(n, l)`` times every candidate on a synthetic matrix of that
+shape with CUDA events and records the fastest in a JSON cache (one entry
+per shape bucket: n rounded to a power of two, padded l, split form);
+``apply(n, l, prec)`` loads the best known setting for the nearest bucket.
+``calibrate_batched()`` fits c0, c1 from single-matrix timings at two row
+lengths.  The cache lives at $PCC_TUNE_CACHE, else
+~/.cache/paper_1605_01584_gb300/tune.json.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+import statistics
+
+from . import (PccError, load, pcc_allpairs_upper, pcc_get_tuning,
+               pcc_set_tuning, pcc_standardize)
+
+DEFAULT_CANDIDATES = {
+    "stage_k": (32, 64),
+    "cluster": (2, 1),
+    "band_rows": (16, 32, 64),
+}
+
+
+def cache_path() -> str:
+    p = os.environ.get("PCC_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache",
+                        "paper_1605_01584_gb300", "tune.json")
+
+
+def bucket(n: int, l: int, prec: str) -> str:
+    """Shape bucket: n to the nearest power of two, l padded to 64."""
+    nb = 1 << max(1, round(math.log2(max(n, 2))))
+    lp = (l + 63) // 64 * 64
+    return f"n{nb}_l{lp}_{prec}"
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def lookup(n: int, l: int, prec: str, cache: dict | None = None):
+    """Best known knobs for (n, l, prec): the exact bucket, else the entry
+    with the same split and padded l whose n is closest (log scale)."""
+    cache = load_cache() if cache is None else cache
+    key = bucket(n, l, prec)
+    if key in cache:
+        return cache[key]["best"]
+    lp = (l + 63) // 64 * 64
+    best, dist = None, None
+    for k, v in cache.items():
+        if not k.endswith(f"_l{lp}_{prec}") or "best" not in v:
+            continue
+        nb = int(k.split("_")[0][1:])
+        d = abs(math.log2(nb) - math.log2(max(n, 2)))
+        if dist is None or d < dist:
+            best, dist = v["best"], d
+    return best
+
+
+def apply(n: int, l: int, prec: str, cache: dict | None = None) -> bool:
+    """Set the library's knobs to the best known values for this shape;
+    False (nothing changed) if the cache has no entry for it."""
+    b = lookup(n, l, prec, cache)
+    if not b:
+        return False
+    pcc_set_tuning(stage_k=b["stage_k"], cluster=b["cluster"],
+                   band_rows=b["band_rows"])
+    return True
+
+
+def _time_ms(fn, reps: int) -> float:
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def tune_pairs(n: int, l: int, prec: str = "auto", candidates=None,
+               reps: int = 5, seed: int = 0, save: bool = True,
+               path: str | None = None) -> dict:
+    """Time every knob combination on an n x l matrix and cache the best."""
+    import torch
+    load()
+    cand = dict(DEFAULT_CANDIDATES)
+    cand.update(candidates or {})
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    X = torch.rand((n, l), device="cuda", generator=g)
+    Z = pcc_standardize(X, prec)
+    resolved = {2: "bf16x3", 3: "fp16x3s", 4: "bf16x1"}.get(
+        Z.info()["prec"], str(prec))
+    R = torch.empty(n * (n - 1) // 2, device="cuda")
+    before = pcc_get_tuning()
+    results = []
+    try:
+        for sk, cl, bd in itertools.product(cand["stage_k"], cand["cluster"],
+                                            cand["band_rows"]):
+            pcc_set_tuning(stage_k=sk, cluster=cl, band_rows=bd)
+            ms = _time_ms(lambda: pcc_allpairs_upper(Z, R), reps)
+            results.append({"stage_k": sk, "cluster": cl, "band_rows": bd,
+                            "ms": ms})
+    finally:
+        pcc_set_tuning(before["stage_k"], before["cluster"],
+                       before["band_rows"])
+    best = min(results, key=lambda r: r["ms"])
+    entry = {"n": n, "l": l, "prec": resolved, "best": best,
+             "all": results}
+    if save:
+        cache = load_cache(path)
+        cache[bucket(n, l, resolved)] = entry
+        save_cache(cache, path)
+    return entry
+
+
+def calibrate_batched(n: int = 8192, ls=(64, 1024), reps: int = 5,
+                      clock_ghz: float | None = None,
+                      apply_now: bool = True) -> dict:
+    """Fit the batched work split's cost model t_unit = c0 + c1 * kblocks *
+    products (in cycles) from single-matrix timings at two row lengths."""
+    import torch
+    load()
+    if clock_ghz is None:
+        clock_ghz = 1.9  # only the ratio c0 : c1 matters to the work split
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    pts = []
+    for l in ls:
+        X = torch.rand((n, l), device="cuda")
+        Z = pcc_standardize(X, "bf16x3")
+        R = torch.empty(n * (n - 1) // 2, device="cuda")
+        ms = _time_ms(lambda: pcc_allpairs_upper(Z, R), reps)
+        m = -(-n // 256)
+        units = m * (m + 1)
+        per_unit_cycles = ms * 1e-3 * clock_ghz * 1e9 * sms / units
+        kblocks = Z.info()["lpad"] // 32
+        pts.append((kblocks * 3, per_unit_cycles))
+    (x0, y0), (x1, y1) = pts
+    c1 = max((y1 - y0) / max(x1 - x0, 1), 1.0)
+    c0 = max(y0 - c1 * x0, 1.0)
+    if apply_now:
+        pcc_set_tuning(cost_c0=c0, cost_c1=c1)
+    return {"c0": c0, "c1": c1, "points": pts, "clock_ghz": clock_ghz}

@@ -11,8 +11,10 @@
 //                  index: an index outside [0, l) is recorded as
 //                  PCC_ERR_INVALID_ARG and read as sample 0, never out of
 //                  bounds).
-//   k_perm_tc      a persistent kernel over work items (128 x 128 tile of
-//                  the triangle, chunk of permutations).  Per item: the A
+//   k_perm_tc      a persistent kernel over work items (chunk of ~48
+//                  permutations, 128 x 128 tile of the triangle), chunk-major
+//                  and column by column so that concurrent CTAs reuse the
+//                  same permuted column panels from L2.  Per item: the A
 //                  rows (z_i, hi and lo) are loaded once into shared memory
 //                  and stay resident; the unpermuted B rows give r_obs and
 //                  then each permutation's B rows (from the workspace, a 3-D
@@ -43,6 +45,20 @@ constexpr int kPTile = kPT * kPK * 2;        // 8 KB: 128 rows x 32 (16-bit)
 constexpr int kPStageB = 2 * kPTile;         // B hi + lo
 constexpr int kPMaxResidentK = 256;          // resident A up to lpad 256
 constexpr int kPSmemBudget = 232448;
+constexpr int64_t kPermChunk = 48;           // permutations per work item
+
+// column-major numbering of the upper triangle of tiles (diagonal in):
+// column x holds tiles (0..x, x), F(x) = x(x+1)/2 tiles before it; the
+// closed-form root is corrected by exact integer tests as in pcc_sched.h
+__device__ __forceinline__ void col_tri_coords(int64_t t, int64_t* y,
+                                               int64_t* x) {
+  int64_t xx = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  if (xx < 0) xx = 0;
+  while (xx > 0 && xx * (xx + 1) / 2 > t) --xx;
+  while ((xx + 1) * (xx + 2) / 2 <= t) ++xx;
+  *x = xx;
+  *y = t - xx * (xx + 1) / 2;
+}
 
 struct PermParams {
   int64_t n;
@@ -73,14 +89,25 @@ struct PCfg {
   static_assert(kStages >= 2, "ring too small");
 };
 
-__global__ void __launch_bounds__(256)
+// One block per (permutation, group of rows).  The permutation is checked
+// and staged in shared memory; each warp then takes one row at a time,
+// copies its hi and lo halves into shared memory with 16-byte loads, and
+// every lane writes 8 permuted elements of each half with one 16-byte
+// store (lpad is a multiple of 64, so rows split into whole 8-element
+// groups).  Shared memory: 4 * lpad bytes of indices and 4 * lpad per warp.
+constexpr int kGatherWarps = 8;
+
+__global__ void __launch_bounds__(kGatherWarps * 32)
     k_perm_gather(const uint16_t* __restrict__ hi,
                   const uint16_t* __restrict__ lo,
                   const int32_t* __restrict__ perms, int64_t n, int64_t l,
                   int64_t lpad, int64_t k_lo, int64_t rows_per_block,
                   uint16_t* __restrict__ ohi, uint16_t* __restrict__ olo,
                   int* __restrict__ status) {
-  extern __shared__ int32_t pi[];
+  extern __shared__ uint8_t gsm[];
+  int32_t* pi = reinterpret_cast<int32_t*>(gsm);              // lpad
+  uint16_t* rows = reinterpret_cast<uint16_t*>(pi + lpad);    // per warp
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t kk = blockIdx.y;
   const int32_t* src = perms + (k_lo + kk) * l;
   bool bad = false;
@@ -94,18 +121,42 @@ __global__ void __launch_bounds__(256)
   }
   if (bad) atomicCAS(status, 0, (int)PCC_ERR_INVALID_ARG);
   __syncthreads();
+  uint16_t* wrow = rows + (size_t)warp * 2 * lpad;  // hi | lo of one row
   const int64_t j0 = blockIdx.x * rows_per_block;
   const int64_t j1 = j0 + rows_per_block < n ? j0 + rows_per_block : n;
-  for (int64_t j = j0; j < j1; ++j) {
-    const uint16_t* rh = hi + j * lpad;
-    const uint16_t* rl = lo + j * lpad;
-    uint16_t* oh = ohi + (kk * n + j) * lpad;
-    uint16_t* ol = olo + (kk * n + j) * lpad;
-    for (int64_t s = threadIdx.x; s < lpad; s += blockDim.x) {
-      const int32_t t = pi[s];
-      oh[s] = t >= 0 ? rh[t] : (uint16_t)0;
-      ol[s] = t >= 0 ? rl[t] : (uint16_t)0;
+  for (int64_t j = j0 + warp; j < j1; j += kGatherWarps) {
+    const uint4* gh = reinterpret_cast<const uint4*>(hi + j * lpad);
+    const uint4* gl = reinterpret_cast<const uint4*>(lo + j * lpad);
+    uint4* sh = reinterpret_cast<uint4*>(wrow);
+    uint4* sl = reinterpret_cast<uint4*>(wrow + lpad);
+    for (int64_t v = lane; v < lpad / 8; v += 32) {
+      sh[v] = gh[v];
+      sl[v] = gl[v];
     }
+    __syncwarp();
+    uint4* oh = reinterpret_cast<uint4*>(ohi + (kk * n + j) * lpad);
+    uint4* ol = reinterpret_cast<uint4*>(olo + (kk * n + j) * lpad);
+    for (int64_t v = lane; v < lpad / 8; v += 32) {
+      uint16_t a[8], b[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int32_t q = pi[v * 8 + t];
+        a[t] = q >= 0 ? wrow[q] : (uint16_t)0;
+        b[t] = q >= 0 ? wrow[lpad + q] : (uint16_t)0;
+      }
+      uint4 ua, ub;
+      ua.x = a[0] | ((uint32_t)a[1] << 16);
+      ua.y = a[2] | ((uint32_t)a[3] << 16);
+      ua.z = a[4] | ((uint32_t)a[5] << 16);
+      ua.w = a[6] | ((uint32_t)a[7] << 16);
+      ub.x = b[0] | ((uint32_t)b[1] << 16);
+      ub.y = b[2] | ((uint32_t)b[3] << 16);
+      ub.z = b[4] | ((uint32_t)b[5] << 16);
+      ub.w = b[6] | ((uint32_t)b[7] << 16);
+      oh[v] = ua;
+      ol[v] = ub;
+    }
+    __syncwarp();
   }
 }
 
@@ -174,12 +225,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
   WaitCtx w{abort_flag, p.status, p.wait_ns};
   const int64_t n = p.n;
 
+  // items run chunk-major, and inside a chunk the tiles of the triangle go
+  // column by column: CTAs working at the same time share the permuted
+  // column panels of the same permutations in L2
+  const int64_t tiles = p.m * (p.m + 1) / 2;
   auto item_coords = [&](int64_t it, int64_t* row0, int64_t* col0, int* k0,
                          int* klen) {
-    const int64_t t = it / p.nchunks;
-    const int c = (int)(it % p.nchunks);
+    const int c = (int)(it / tiles);
+    const int64_t t = it % tiles;
     int64_t yt, xt;
-    tri_coords(p.m, t, &yt, &xt);
+    col_tri_coords(t, &yt, &xt);
     *row0 = yt * kPT;
     *col0 = xt * kPT;
     *k0 = c * p.chunk;
@@ -455,29 +510,41 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
   const int64_t m = (n + kPT - 1) / kPT;
   const int64_t tiles = m * (m + 1) / 2;
   const int sms = num_sms(Z->device);
+  if ((size_t)lpad * 4 + (size_t)kGatherWarps * 4 * lpad > 200 * 1024)
+    return PCC_ERR_UNSUPPORTED;  // rows longer than the gather stages
+  cudaError_t e = cudaSuccess;
   for (int64_t kb0 = k0; kb0 < k1; kb0 += kb_alloc) {
     const int64_t kbatch = (k1 - kb0) < kb_alloc ? (k1 - kb0) : kb_alloc;
     uint16_t* wl = wh + (size_t)kbatch * (size_t)n * (size_t)lpad;
     // gather the permuted halves of the batch
-    const int64_t rpb = 16;
+    const int64_t rpb = 64;
     dim3 g((unsigned)((n + rpb - 1) / rpb), (unsigned)kbatch, 1);
-    k_perm_gather<<<g, 256, (size_t)lpad * sizeof(int32_t), s>>>(
+    const size_t gsmem = (size_t)lpad * 4 + (size_t)kGatherWarps * 4 * lpad;
+    if (gsmem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_perm_gather,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gsmem);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    k_perm_gather<<<g, kGatherWarps * 32, gsmem, s>>>(
         static_cast<const uint16_t*>(Z->hi),
         static_cast<const uint16_t*>(Z->lo), d_perms, n, Z->l, lpad, kb0, rpb,
         wh, wl, Z->status);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e);
     CUtensorMap ph, pl;
     if (!encode_tmap_3d_u16(&ph, wh, kbatch, n, lpad, kPT, kPK, bf16) ||
         !encode_tmap_3d_u16(&pl, wl, kbatch, n, lpad, kPT, kPK, bf16))
       return PCC_ERR_CUDA;
-    // chunks: enough work items for about 8 per SM
-    int64_t nchunks = (8 * (int64_t)sms + tiles - 1) / tiles;
-    if (nchunks > kbatch) nchunks = kbatch;
-    if (nchunks < 1) nchunks = 1;
-    int64_t chunk = (kbatch + nchunks - 1) / nchunks;
-    if (chunk > 65535) chunk = 65535;  // 16-bit counters
-    nchunks = (kbatch + chunk - 1) / chunk;
+    // chunks of about kPermChunk permutations: short enough that the
+    // permuted panels in flight fit in L2, long enough that r_obs (one
+    // extra pass per item) stays a few percent; and at least ~8 items per SM
+    int64_t chunk = kPermChunk;
+    if (tiles * ((kbatch + chunk - 1) / chunk) < 8 * (int64_t)sms)
+      chunk = (kbatch * tiles + 8 * (int64_t)sms - 1) / (8 * (int64_t)sms);
+    if (chunk < 1) chunk = 1;
+    if (chunk > kbatch) chunk = kbatch;
+    const int64_t nchunks = (kbatch + chunk - 1) / chunk;
     PermParams p;
     p.n = n;
     p.m = m;

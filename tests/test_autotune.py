@@ -1,0 +1,51 @@
+"""The tuner's cache logic (CPU) and one small tuning run (GPU)."""
+import numpy as np
+import pytest
+
+from paper_1605_01584_gb300 import autotune
+
+
+def test_bucket_and_nearest_lookup(tmp_path):
+    p = str(tmp_path / "t.json")
+    assert autotune.bucket(65536, 512, "bf16x3") == "n65536_l512_bf16x3"
+    assert autotune.bucket(50000, 500, "bf16x3") == "n65536_l512_bf16x3"
+    assert autotune.bucket(40000, 33, "fp16x3s") == "n32768_l64_fp16x3s"
+    cache = {
+        "n16384_l512_bf16x3": {"best": {"stage_k": 64, "cluster": 1,
+                                        "band_rows": 16}},
+        "n65536_l512_bf16x3": {"best": {"stage_k": 32, "cluster": 2,
+                                        "band_rows": 32}},
+    }
+    autotune.save_cache(cache, p)
+    c = autotune.load_cache(p)
+    assert c == cache
+    assert autotune.lookup(65536, 512, "bf16x3", c)["stage_k"] == 32
+    assert autotune.lookup(20000, 512, "bf16x3", c)["stage_k"] == 64
+    assert autotune.lookup(20000, 1024, "bf16x3", c) is None
+    assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
+
+
+@pytest.mark.gpu
+def test_tune_small_shape_and_apply(pcc_gpu, tmp_path):
+    import torch
+    pcc = pcc_gpu
+    p = str(tmp_path / "tune.json")
+    before = pcc.pcc_get_tuning()
+    e = autotune.tune_pairs(2048, 128, "bf16x3", reps=2, path=p,
+                            candidates={"band_rows": (8, 32)})
+    assert len(e["all"]) == 8 and e["best"]["ms"] > 0
+    assert pcc.pcc_get_tuning() == before  # tuning run restores the knobs
+    X = torch.rand((2048, 128), device="cuda")
+    Z = pcc.pcc_standardize(X, "bf16x3")
+    R0 = torch.empty(2048 * 2047 // 2, device="cuda")
+    pcc.pcc_allpairs_upper(Z, R0)
+    try:
+        assert autotune.apply(2048, 128, "bf16x3",
+                              autotune.load_cache(p))
+        R1 = torch.empty_like(R0)
+        pcc.pcc_allpairs_upper(Z, R1)
+        torch.cuda.synchronize()
+        assert torch.equal(R0, R1)  # knobs never change results
+    finally:
+        pcc.pcc_set_tuning(before["stage_k"], before["cluster"],
+                           before["band_rows"])

@@ -1,0 +1,129 @@
+"""Parity at full workload sizes, in the launch configuration bench.py times,
+on outputs the oracle can compute one by one.
+
+  precision workload  n=16384 x l=1024: max|dr| of every stored form on
+                      10^6 uniformly sampled pairs plus every pair of the
+                      planted modules (where |r| -> 1 and the split error
+                      peaks); split forms and FP32 must be <= 1e-5, the
+                      single-BF16 form is reported only.
+  output-bound        n=65536 x l=512: the fused packed + edge pass; max|dr|
+                      on 10^6 sampled pairs plus module pairs, and the edge
+                      list of 48 sampled row panels equal to the oracle's
+                      outside the +-1e-5 band around tau = 0.8.
+The measured errors are written to tests' stdout (pytest -s) as JSON.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _sample_pairs(n, k, seed, mod):
+    rng = np.random.default_rng(seed)
+    J = rng.integers(0, n * (n - 1) // 2, k)
+    # inverse of the packed numbering (row = largest i with base <= J)
+    i = np.floor((2 * n - 1 - np.sqrt((2 * n - 1) ** 2 - 8 * J)) / 2)
+    i = i.astype(np.int64)
+    start = i * (2 * n - i - 1) // 2
+    i = np.where(start > J, i - 1, i)
+    start = i * (2 * n - i - 1) // 2
+    nxt = (i + 1) * (2 * n - i - 2) // 2
+    i = np.where(nxt <= J, i + 1, i)
+    start = i * (2 * n - i - 1) // 2
+    j = J - start + i + 1
+    I, Jc = [i], [j]
+    for m in range(min(mod.max() + 1, 40)):
+        g = np.nonzero(mod == m)[0]
+        a, b = np.triu_indices(len(g), 1)
+        I.append(g[a])
+        Jc.append(g[b])
+    I = np.concatenate(I)
+    Jc = np.concatenate(Jc)
+    assert np.all(I < Jc) and np.all(Jc < n)
+    return I, Jc
+
+
+def _gather(R, n, I, J):
+    torch = _torch()
+    idx = torch.from_numpy(I * (2 * n - I - 1) // 2 + (J - I - 1)).cuda()
+    return R[idx].cpu().numpy().astype(np.float64)
+
+
+def test_precision_workload_every_form(pcc_gpu):
+    torch = _torch()
+    pcc = pcc_gpu
+    n, l = 16384, 1024
+    X, mod = synth.counts_log(n, l, 2, return_modules=True)
+    I, J = _sample_pairs(n, 1_000_000, 102, mod)
+    want = oracle.pcc_pairs(X, I, J)
+    ok = ~np.isnan(want)
+    Xd = torch.from_numpy(X).cuda()
+    R = torch.empty(n * (n - 1) // 2, device="cuda")
+    report = {}
+    for prec in ("bf16x3", "fp16x3s", "bf16x1", "fp32", "auto"):
+        Z = pcc.pcc_standardize(Xd, prec)
+        pcc.pcc_allpairs_upper(Z, R)
+        assert pcc.pcc_sync_status(Z) == 0
+        got = _gather(R, n, I, J)
+        assert np.array_equal(np.isnan(got), np.isnan(want)), prec
+        report[prec] = float(np.max(np.abs(got[ok] - want[ok])))
+        Z.close()
+    print(json.dumps({"precision_workload_max_abs_dr": report,
+                      "pairs_checked": int(ok.sum())}))
+    for prec in ("bf16x3", "fp16x3s", "fp32", "auto"):
+        assert report[prec] <= 1e-5, (prec, report[prec])
+    assert report["bf16x1"] <= 2e-2
+
+
+def test_output_bound_workload_fused(pcc_gpu):
+    torch = _torch()
+    pcc = pcc_gpu
+    n, l, tau = 65536, 512, 0.8
+    X, mod = synth.counts_log(n, l, 3, return_modules=True)
+    Xd = torch.from_numpy(X).cuda()
+    Z = pcc.pcc_standardize(Xd, "auto")
+    R = torch.empty(n * (n - 1) // 2, device="cuda")
+    cap = 1 << 24
+    E = torch.empty(cap * pcc.EDGE_BYTES, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pcc.pcc_threshold_edges(Z, tau, E, cap, cnt, R)
+    assert pcc.pcc_sync_status(Z) == 0
+    c = int(cnt.item())
+    I, J = _sample_pairs(n, 1_000_000, 103, mod)
+    want = oracle.pcc_pairs(X, I, J)
+    got = _gather(R, n, I, J)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    err = float(np.max(np.abs(got[ok] - want[ok])))
+    # edges of 48 sampled row panels of 16 rows against the oracle
+    ei, ej, er = pcc.edges_view(E, min(c, cap))
+    rng = np.random.default_rng(203)
+    panels = rng.choice(n // 16, 48, replace=False) * 16
+    band_extra = band_missing = checked = 0
+    for r0 in panels:
+        oi, oj, orr = oracle.edges(X, tau, int(r0), int(r0) + 16)
+        want_e = set(zip(oi.tolist(), oj.tolist()))
+        sel = (ei >= r0) & (ei < r0 + 16)
+        got_e = set(zip(ei[sel].tolist(), ej[sel].tolist()))
+        assert len(got_e) == int(sel.sum())
+        for a, b in got_e ^ want_e:
+            rr = oracle.pcc_pairs(X, [a], [b])[0]
+            assert abs(abs(rr) - tau) <= 1e-5, (a, b, rr)
+            band_extra += (a, b) in got_e
+            band_missing += (a, b) in want_e
+        checked += len(want_e)
+    print(json.dumps({"output_bound_max_abs_dr": err, "edges_total": c,
+                      "edges_checked": checked, "band_extra": band_extra,
+                      "band_missing": band_missing}))
+    assert err <= 1e-5
+    assert c < cap
