@@ -132,7 +132,7 @@ class ClockSampler:
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("tc_pairs.cu", "pcc_ptx.cuh", "pcc_sched.h"):
+    for f in ("tc_pairs.cu", "tc_epilogue.cuh", "pcc_ptx.cuh", "pcc_sched.h"):
         h.update(open(os.path.join(ROOT, "paper_1605_01584_gb300", "csrc",
                                    f), "rb").read())
     return h.hexdigest()[:16]

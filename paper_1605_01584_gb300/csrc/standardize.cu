@@ -42,6 +42,25 @@ __device__ __forceinline__ float dev_ff(float x, float mh, float ml) {
   return s + (e - ml);
 }
 
+// (s, c) += x: Knuth's TwoSum adds the exact rounding error of s + x to
+// the compensation c (explicit _rn operations keep the compiler from
+// reassociating or contracting them).
+__device__ __forceinline__ void ff_add(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  s = t;
+  c = __fadd_rn(c, err);
+}
+
+// (s, c) += d*d with the product split exactly: p = fl(d*d), e = d*d - p.
+__device__ __forceinline__ void ff_add_sq(float& s, float& c, float d) {
+  const float p = __fmul_rn(d, d);
+  const float e = fmaf(d, d, -p);
+  ff_add(s, c, p);
+  c = __fadd_rn(c, e);
+}
+
 template <typename TX, int MODE>
 __global__ void __launch_bounds__(256)
     k_standardize(const TX* __restrict__ X, int64_t n, int64_t l, int64_t ldx,
@@ -126,55 +145,83 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// FP32 input, rows 16-B aligned (ldx % 4 == 0): float4 loads, four
-// independent FP64 accumulators per lane, and the deviations of pass 2
-// formed in FP32 pairs (dev_ff, one rounding) before their squares are
-// accumulated in FP64, so a row costs 2 FP64 operations per element.
+// FP32 input, rows 16-B aligned (ldx % 4 == 0): float4 loads.  GB300 has
+// little FP64 throughput, so each lane forms its partial sums of x and of
+// d^2 as error-free float pairs (TwoSum, exact FMA-split squares, relative
+// error ~2^-44) and only those partials are converted and summed across the
+// row in FP64: the row mean and centred sum of squares are FP64 values at a
+// cost of a few FP64 operations per lane instead of per element.
+// sum over the 8 lanes of an 8-lane group (xor offsets stay in the group)
+__device__ __forceinline__ double group8_sum(double v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256)
     k_standardize_f32v(const float* __restrict__ X, int64_t n, int64_t l,
-                       int64_t ldx, int64_t lpad, float zscale,
+                       int64_t ldx, int64_t lpad, double inv_l, float zscale,
                        void* __restrict__ out0, void* __restrict__ out1,
                        uint8_t* __restrict__ flags) {
+  // a warp standardizes 4 rows at a time, 8 lanes per row: the per-row
+  // FP64 work (3 reduction steps, mean, 1/sqrt) is shared by 4 rows
   const int lane = threadIdx.x & 31;
+  const int grp = lane >> 3, gl = lane & 7;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t l4 = l & ~int64_t(3);
-  for (int64_t i = warp0; i < n; i += nwarps) {
-    const float* x = X + i * ldx;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    for (int64_t k = 4 * lane; k < l4; k += 128) {
+  for (int64_t i0 = 4 * warp0; i0 < n; i0 += 4 * nwarps) {
+    const int64_t i = i0 + grp;
+    const bool live = i < n;  // dead groups run along for the shuffles
+    const float* x = X + (live ? i : i0) * ldx;
+    // pass 1: float-pair partial sums, merged exactly in FP32 and summed
+    // over the row's 8 lanes in FP64
+    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t k = 4 * gl; k < l4; k += 32) {
       const float4 v = *reinterpret_cast<const float4*>(x + k);
-      s0 += (double)v.x;
-      s1 += (double)v.y;
-      s2 += (double)v.z;
-      s3 += (double)v.w;
+      ff_add(sh[0], sl[0], v.x);
+      ff_add(sh[1], sl[1], v.y);
+      ff_add(sh[2], sl[2], v.z);
+      ff_add(sh[3], sl[3], v.w);
     }
-    for (int64_t k = l4 + lane; k < l; k += 32) s0 += (double)x[k];
-    const double mean = warp_sum((s0 + s1) + (s2 + s3)) / (double)l;
+    for (int64_t k = l4 + gl; k < l; k += 8) ff_add(sh[0], sl[0], x[k]);
+#pragma unroll
+    for (int t = 1; t < 4; ++t) {
+      ff_add(sh[0], sl[0], sh[t]);
+      sl[0] = __fadd_rn(sl[0], sl[t]);
+    }
+    const double mean =
+        group8_sum((double)sh[0] + (double)sl[0]) * inv_l;
     const float mh = (float)mean, ml = (float)(mean - (double)mh);
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
-    for (int64_t k = 4 * lane; k < l4; k += 128) {
+    // pass 2: deviations (one rounding), exact squares, float-pair sums
+    float qh[4] = {0.f, 0.f, 0.f, 0.f}, ql[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t k = 4 * gl; k < l4; k += 32) {
       const float4 v = *reinterpret_cast<const float4*>(x + k);
-      const double d0 = (double)dev_ff(v.x, mh, ml);
-      const double d1 = (double)dev_ff(v.y, mh, ml);
-      const double d2 = (double)dev_ff(v.z, mh, ml);
-      const double d3 = (double)dev_ff(v.w, mh, ml);
-      q0 = fma(d0, d0, q0);
-      q1 = fma(d1, d1, q1);
-      q2 = fma(d2, d2, q2);
-      q3 = fma(d3, d3, q3);
+      ff_add_sq(qh[0], ql[0], dev_ff(v.x, mh, ml));
+      ff_add_sq(qh[1], ql[1], dev_ff(v.y, mh, ml));
+      ff_add_sq(qh[2], ql[2], dev_ff(v.z, mh, ml));
+      ff_add_sq(qh[3], ql[3], dev_ff(v.w, mh, ml));
     }
-    for (int64_t k = l4 + lane; k < l; k += 32) {
-      const double d = (double)dev_ff(x[k], mh, ml);
-      q0 = fma(d, d, q0);
+    for (int64_t k = l4 + gl; k < l; k += 8)
+      ff_add_sq(qh[0], ql[0], dev_ff(x[k], mh, ml));
+#pragma unroll
+    for (int t = 1; t < 4; ++t) {
+      ff_add(qh[0], ql[0], qh[t]);
+      ql[0] = __fadd_rn(ql[0], ql[t]);
     }
-    const double q = warp_sum((q0 + q1) + (q2 + q3));
+    const double q = group8_sum((double)qh[0] + (double)ql[0]);
     const bool bad = !(q > 0.0) || !isfinite(q) || !isfinite(mean);
-    if (lane == 0) flags[i] = bad ? 1 : 0;
-    const double inv = bad ? 0.0 : 1.0 / sqrt(q);
+    if (live && gl == 0) flags[i] = bad ? 1 : 0;
+    // 1/sqrt(q): FP32 estimate, one Newton step in FP64 (error ~2^-44)
+    double inv = 0.0;
+    if (!bad) {
+      const double y = (double)rsqrtf((float)q);
+      inv = y * (1.5 - 0.5 * q * y * y);
+    }
     const float invf = (float)(inv * (double)zscale);
-    for (int64_t k = 4 * lane; k < lpad; k += 128) {
+    if (!live) continue;
+    for (int64_t k = 4 * gl; k < lpad; k += 32) {
       float z[4] = {0.f, 0.f, 0.f, 0.f};
       if (!bad) {
         if (k + 3 < l) {
@@ -230,8 +277,9 @@ __global__ void __launch_bounds__(256)
 template <int MODE>
 void launch_f32v(const float* X, int64_t ldx, pcc_zmat* Z, int blocks,
                  float zscale, void* o0, void* o1, cudaStream_t s) {
-  k_standardize_f32v<MODE><<<blocks, 256, 0, s>>>(X, Z->n, Z->l, ldx, Z->lpad,
-                                                  zscale, o0, o1, Z->flags);
+  k_standardize_f32v<MODE><<<blocks, 256, 0, s>>>(
+      X, Z->n, Z->l, ldx, Z->lpad, 1.0 / (double)Z->l, zscale, o0, o1,
+      Z->flags);
 }
 
 template <typename TX>
