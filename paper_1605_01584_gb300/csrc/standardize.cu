@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// FP32 input, rows 16-B aligned (ldx % 4 == 0): float4 loads.  GB300 has
+// FP32 input (16-byte loads when rows are 16-B aligned).  GB300 has
 // little FP64 throughput, so each lane forms its partial sums of x and of
 // d^2 as error-free float pairs (TwoSum, exact FMA-split squares, relative
 // error ~2^-44) and only those partials are converted and summed across the
@@ -158,7 +158,17 @@ __device__ __forceinline__ double group8_sum(double v) {
   return v;
 }
 
-template <int MODE>
+// four consecutive floats at x + k (ALIGNED: one 16-byte load)
+template <bool ALIGNED>
+__device__ __forceinline__ float4 load4(const float* x, int64_t k) {
+  if constexpr (ALIGNED) {
+    return *reinterpret_cast<const float4*>(x + k);
+  } else {
+    return make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+  }
+}
+
+template <int MODE, bool ALIGNED>
 __global__ void __launch_bounds__(256)
     k_standardize_f32v(const float* __restrict__ X, int64_t n, int64_t l,
                        int64_t ldx, int64_t lpad, double inv_l, float zscale,
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(256)
     // over the row's 8 lanes in FP64
     float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
     for (int64_t k = 4 * gl; k < l4; k += 32) {
-      const float4 v = *reinterpret_cast<const float4*>(x + k);
+      const float4 v = load4<ALIGNED>(x, k);
       ff_add(sh[0], sl[0], v.x);
       ff_add(sh[1], sl[1], v.y);
       ff_add(sh[2], sl[2], v.z);
@@ -197,7 +207,7 @@ __global__ void __launch_bounds__(256)
     // pass 2: deviations (one rounding), exact squares, float-pair sums
     float qh[4] = {0.f, 0.f, 0.f, 0.f}, ql[4] = {0.f, 0.f, 0.f, 0.f};
     for (int64_t k = 4 * gl; k < l4; k += 32) {
-      const float4 v = *reinterpret_cast<const float4*>(x + k);
+      const float4 v = load4<ALIGNED>(x, k);
       ff_add_sq(qh[0], ql[0], dev_ff(v.x, mh, ml));
       ff_add_sq(qh[1], ql[1], dev_ff(v.y, mh, ml));
       ff_add_sq(qh[2], ql[2], dev_ff(v.z, mh, ml));
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(256)
       float z[4] = {0.f, 0.f, 0.f, 0.f};
       if (!bad) {
         if (k + 3 < l) {
-          const float4 v = *reinterpret_cast<const float4*>(x + k);
+          const float4 v = load4<ALIGNED>(x, k);
           z[0] = dev_ff(v.x, mh, ml) * invf;
           z[1] = dev_ff(v.y, mh, ml) * invf;
           z[2] = dev_ff(v.z, mh, ml) * invf;
@@ -277,9 +287,16 @@ __global__ void __launch_bounds__(256)
 template <int MODE>
 void launch_f32v(const float* X, int64_t ldx, pcc_zmat* Z, int blocks,
                  float zscale, void* o0, void* o1, cudaStream_t s) {
-  k_standardize_f32v<MODE><<<blocks, 256, 0, s>>>(
-      X, Z->n, Z->l, ldx, Z->lpad, 1.0 / (double)Z->l, zscale, o0, o1,
-      Z->flags);
+  const bool aligned =
+      (ldx % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  if (aligned)
+    k_standardize_f32v<MODE, true><<<blocks, 256, 0, s>>>(
+        X, Z->n, Z->l, ldx, Z->lpad, 1.0 / (double)Z->l, zscale, o0, o1,
+        Z->flags);
+  else
+    k_standardize_f32v<MODE, false><<<blocks, 256, 0, s>>>(
+        X, Z->n, Z->l, ldx, Z->lpad, 1.0 / (double)Z->l, zscale, o0, o1,
+        Z->flags);
 }
 
 template <typename TX>
@@ -291,8 +308,7 @@ cudaError_t launch_mode(const TX* X, int64_t ldx, pcc_zmat* Z,
   if (blocks > cap) blocks = cap;
   const float zscale = (float)ldexp(1.0, Z->scale_exp);
   if constexpr (sizeof(TX) == 4) {
-    if ((ldx % 4) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
-        Z->prec != PCC_PREC_FP64) {
+    if (Z->prec != PCC_PREC_FP64) {
       const float* Xf = reinterpret_cast<const float*>(X);
       switch (Z->prec) {
         case PCC_PREC_BF16X3:

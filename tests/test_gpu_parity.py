@@ -258,3 +258,23 @@ def test_invalid_arguments(pcc_gpu):
         pcc_gpu.pcc_allpairs_upper(Z, R, 0, Z.num_tiles() + 1)
     with pytest.raises(pcc_gpu.PccError):
         pcc_gpu.pcc_allpairs_upper(Z, R.double())
+
+
+def test_sharded_ranks_cover_the_triangle(pcc_gpu):
+    """Section III-D's equal tile ranges, one call per (simulated) rank into
+    the same output: every pair is written exactly by its owner."""
+    from paper_1605_01584_gb300 import shard
+    torch = _torch()
+    X = _data(1500, 96, seed=8)
+    whole, Z = gpu_allpairs(pcc_gpu, X, "auto")
+    R = torch.full((1500 * 1499 // 2,), 7.0, device="cuda")
+    covered = 0
+    for rank in range(3):
+        b, e = shard.allpairs_sharded(Z, R, rank, 3)
+        covered += e - b
+    assert covered == Z.num_tiles()
+    got = R.cpu().numpy().astype(np.float64)
+    assert not np.any(got == 7.0)
+    assert np.array_equal(np.isnan(got), np.isnan(whole))
+    ok = ~np.isnan(whole)
+    assert np.array_equal(got[ok], whole[ok])
