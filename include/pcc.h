@@ -236,6 +236,15 @@ pcc_status pcc_get_tuning(int32_t *stage_k, int32_t *cluster,
  * status word and the kernel returns early instead of hanging. */
 pcc_status pcc_set_wait_limit_ns(uint64_t ns);
 
+/* Test hook for the failure path (the paper has no counterpart): while
+ * enabled, the TMA producer of the tensor-core pair kernel issues no loads,
+ * so every CTA's first operand wait runs out after the wait limit; the
+ * kernel records PCC_ERR_TIMEOUT, frees its TMEM and returns, and the CUDA
+ * context stays usable.  Nothing faults or hangs: no copy or MMA is in
+ * flight when the CTAs unwind.  Pair with a short pcc_set_wait_limit_ns.
+ * Never enable it outside tests. */
+pcc_status pcc_debug_drop_loads(int32_t enable);
+
 /* ------------------------------------------------------------------ */
 /* Numbering helpers (host functions, Section III-B/C).                */
 /* ------------------------------------------------------------------ */

@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "pcc_allpairs_upper_noalloc": (_ST, [_P, _I64, _I64, _I64, _I32, _P,
                                              _P, _P]),
         "pcc_set_wait_limit_ns": (_ST, [_U64]),
+        "pcc_debug_drop_loads": (_ST, [_I32]),
         "pcc_set_tuning": (_ST, [_I32, _I32, _I32, ctypes.c_double,
                                  ctypes.c_double]),
         "pcc_get_tuning": (_ST, [_P, _P, _P, _P, _P]),
@@ -242,6 +243,12 @@ def pcc_sync_status(Z: Zmat, stream=None) -> int:
 
 def pcc_set_wait_limit_ns(ns: int):
     _check(load().pcc_set_wait_limit_ns(int(ns)), "pcc_set_wait_limit_ns")
+
+
+def pcc_debug_drop_loads(enable: bool):
+    """Test hook: make the pair kernel's operand waits run out (see pcc.h)."""
+    _check(load().pcc_debug_drop_loads(1 if enable else 0),
+           "pcc_debug_drop_loads")
 
 
 def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,

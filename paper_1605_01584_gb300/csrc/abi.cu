@@ -87,6 +87,11 @@ int num_sms(int device) {
 uint64_t wait_limit_ns() { return g_wait_ns.load(); }
 
 namespace {
+std::atomic<int> g_drop_loads{0};
+}
+bool debug_drop_loads() { return g_drop_loads.load() != 0; }
+
+namespace {
 std::mutex g_tune_mu;
 TcTuning g_tune = [] {
   TcTuning t;
@@ -414,6 +419,11 @@ pcc_status pcc_sync_status(pcc_zmat* Z, void* stream) {
   if (e != cudaSuccess) return PCC_ERR_CUDA;
   if (v != 0) cudaMemset(Z->status, 0, sizeof(int));
   return (pcc_status)v;
+}
+
+pcc_status pcc_debug_drop_loads(int32_t enable) {
+  g_drop_loads.store(enable ? 1 : 0);
+  return PCC_OK;
 }
 
 pcc_status pcc_set_wait_limit_ns(uint64_t ns) {

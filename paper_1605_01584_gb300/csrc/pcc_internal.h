@@ -37,6 +37,7 @@ constexpr int kLpadAlign = 64;
 bool is_split(pcc_prec p);
 int num_sms(int device);
 uint64_t wait_limit_ns();
+bool debug_drop_loads();  // test hook of pcc_debug_drop_loads
 cudaError_t ensure_func_smem(const void* func, int bytes);
 pcc_status cuda_status(cudaError_t e);
 

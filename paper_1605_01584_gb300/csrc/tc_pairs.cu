@@ -74,6 +74,8 @@ struct TcParams {
   uint64_t cap;
   int* status;
   uint64_t wait_ns;
+  int drop_loads;    // test hook: the producer issues no loads, so the
+                     // first operand wait runs out (pcc_debug_drop_loads)
 };
 
 // KB = K per ring stage: 64 (one 128-B swizzle row of 16-bit elements, 2
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t last_phase[S];
       for (int s = 0; s < S; ++s) last_phase[s] = 0;
       const uint64_t pol = l2_policy_evict_last();
-      for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
+      for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end && !p.drop_loads;
+           u += gridDim.x) {
         int64_t row0, col0;
         unit_coords(&cur, p, u, &row0, &col0);
         // a cluster's CTAs run their units in lockstep (they share B), so
@@ -486,6 +489,7 @@ cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
   p.cap = cap;
   p.status = Z->status;
   p.wait_ns = wait_limit_ns();
+  p.drop_loads = debug_drop_loads() ? 1 : 0;
   const int64_t units = p.u_end - p.u_begin;
   int grid = num_sms(Z->device);
   if (units < grid) grid = (int)units;

@@ -1,0 +1,56 @@
+"""Failure detection without a GPU fault: a bounded device wait that runs
+out is reported as PCC_ERR_TIMEOUT and the context stays usable; an
+allocation that cannot succeed is reported as PCC_ERR_OOM."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("cluster", [2, 1])
+def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster):
+    import torch
+    pcc = pcc_gpu
+    X = torch.from_numpy(synth.counts_log(1200, 64, 31)).cuda()
+    Z = pcc.pcc_standardize(X, "bf16x3")
+    n = 1200
+    R = torch.full((n * (n - 1) // 2,), 7.0, device="cuda")
+    before = pcc.pcc_get_tuning()
+    pcc.pcc_set_tuning(cluster=cluster)
+    try:
+        pcc.pcc_set_wait_limit_ns(200_000_000)  # 0.2 s
+        pcc.pcc_debug_drop_loads(True)
+        pcc.pcc_allpairs_upper(Z, R)
+        assert pcc.pcc_sync_status(Z) == pcc.PCC_ERR_TIMEOUT
+    finally:
+        pcc.pcc_debug_drop_loads(False)
+        pcc.pcc_set_wait_limit_ns(4_000_000_000)
+        pcc.pcc_set_tuning(cluster=before["cluster"])
+    # the status word was cleared by the read and the context still works
+    assert pcc.pcc_sync_status(Z) == 0
+    pcc.pcc_allpairs_upper(Z, R)
+    assert pcc.pcc_sync_status(Z) == 0
+    got = R.cpu().numpy()
+    ref = torch.full_like(R, 7.0)
+    Z32 = pcc.pcc_standardize(X, "fp32")
+    pcc.pcc_allpairs_upper(Z32, ref)
+    ref = ref.cpu().numpy()
+    ok = ~np.isnan(ref)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    assert np.max(np.abs(got[ok] - ref[ok])) <= 1e-5
+
+
+def test_allocation_failure_is_reported(pcc_gpu):
+    import torch
+    pcc = pcc_gpu
+    X = torch.zeros((4, 4), device="cuda")
+    # a standardized matrix of 2^31-1 rows x 2^20 samples needs ~8 PB: the
+    # allocation fails before anything reads X
+    with pytest.raises(pcc.PccError) as e:
+        pcc.pcc_standardize(X, "bf16x3", n=(1 << 31) - 1, l=1 << 20,
+                            ldx=1 << 20)
+    assert e.value.status == pcc.PCC_ERR_OOM
+    Z = pcc.pcc_standardize(X + torch.arange(4.0, device="cuda"), "bf16x3")
+    assert pcc.pcc_sync_status(Z) == 0
