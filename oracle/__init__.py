@@ -52,6 +52,14 @@ def _load(path):
                                _I64, _I64, _P, _P, _P]
     L.oracle_perm_counts.argtypes = [_P, _I64, _I64, _I64, _I64, _P, _I64,
                                      _P, _P, ctypes.c_double, _P, _P, _P]
+    L.oracle_cross_job_index.restype = _I64
+    L.oracle_cross_job_index.argtypes = [_I64, _I64, _I64, _I64]
+    L.oracle_cross_job_coords.restype = ctypes.c_int
+    L.oracle_cross_job_coords.argtypes = [_I64, _I64, _I64, _P, _P]
+    L.oracle_cross_rows.argtypes = [_P, _I64, _I64, _P, _I64, _I64, _I64,
+                                    _I64, _I64, _P]
+    L.oracle_cross_pairs.argtypes = [_P, _I64, _I64, _P, _I64, _I64, _I64,
+                                     _I64, _P, _P, _P]
     L.oracle_num_threads.restype = ctypes.c_int
     return L
 
@@ -193,3 +201,48 @@ def perm_counts(X, perms, I, J, delta: float = 0.0, L=None):
                                     _ptr(I), _ptr(J), float(delta), _ptr(c),
                                     _ptr(clo), _ptr(chi))
     return c, clo, chi
+
+
+def cross_job_index(nrow: int, ncol: int, y: int, x: int, L=None) -> int:
+    """Eq. (7): J = y * ncol + x on an nrow x ncol job matrix."""
+    return int((L or lib()).oracle_cross_job_index(nrow, ncol, y, x))
+
+
+def cross_job_coords(nrow: int, ncol: int, J: int, L=None):
+    """Eq. (8): (y, x) of job J (by search)."""
+    y = ctypes.c_int64()
+    x = ctypes.c_int64()
+    rc = (L or lib()).oracle_cross_job_coords(nrow, ncol, J, ctypes.byref(y),
+                                              ctypes.byref(x))
+    if rc != 0:
+        raise ValueError(f"job id {J} out of range for {nrow} x {ncol}")
+    return int(y.value), int(x.value)
+
+
+def cross_rows(X, Y, i0: int = 0, i1: int | None = None, L=None):
+    """Eq. (1) for (x_i, y_j), i in [i0, i1), all j: (i1 - i0) x ny."""
+    X = _f64(X)
+    Y = _f64(Y)
+    nx, l = X.shape
+    ny, ly = Y.shape
+    assert ly == l
+    i1 = nx if i1 is None else i1
+    out = np.empty((i1 - i0, ny))
+    (L or lib()).oracle_cross_rows(_ptr(X), nx, l, _ptr(Y), ny, l, l, i0, i1,
+                                   _ptr(out))
+    return out
+
+
+def cross_pairs(X, Y, I, J, L=None) -> np.ndarray:
+    """Eq. (1) for (x_{I[p]}, y_{J[p]})."""
+    X = _f64(X)
+    Y = _f64(Y)
+    nx, l = X.shape
+    ny, ly = Y.shape
+    assert ly == l
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    r = np.empty(I.size)
+    (L or lib()).oracle_cross_pairs(_ptr(X), nx, l, _ptr(Y), ny, l, l, I.size,
+                                    _ptr(I), _ptr(J), _ptr(r))
+    return r

@@ -32,6 +32,11 @@
  *                           Eq. (16)-(19); inverse again by search.
  *   oracle_edges         -- pairs with |r| >= tau (co-expression network
  *                           edges, Section I).
+ *   oracle_cross_*       -- non-symmetric all-pairs (Section III-B, the
+ *                           job matrix of Eq. (7)-(8)) between the rows of
+ *                           two matrices X (nx x l) and Y (ny x l): Eq. (1)
+ *                           for every (x_i, y_j); jobs numbered row-major,
+ *                           J = i*ny + j (Eq. (7)), inverse by search.
  *   oracle_perm_counts   -- permutation test (Section IV-A): for each of P
  *                           sample permutations pi_k, Eq. (1) on
  *                           (x_i, x_j o pi_k) with (x_j o pi_k)[s] =
@@ -341,6 +346,90 @@ void oracle_perm_counts(const double *X, int64_t n, int64_t l, int64_t ldx,
     }
     free(mean);
     free(ssq);
+}
+
+/* ------------------------------------------------------------------ */
+/* Non-symmetric all-pairs between two matrices (Eq. (7)-(8))          */
+/* ------------------------------------------------------------------ */
+
+/* Eq. (7) on an nrow x ncol job matrix: J = y*ncol + x; -1 outside it */
+int64_t oracle_cross_job_index(int64_t nrow, int64_t ncol, int64_t y,
+                               int64_t x)
+{
+    if (y < 0 || y >= nrow || x < 0 || x >= ncol)
+        return -1;
+    return y * ncol + x;
+}
+
+/* inverse of Eq. (7) by search: y is the largest row with y*ncol <= J */
+int oracle_cross_job_coords(int64_t nrow, int64_t ncol, int64_t J, int64_t *y,
+                            int64_t *x)
+{
+    if (nrow < 1 || ncol < 1 || J < 0 || J >= nrow * ncol)
+        return -1;
+    int64_t lo = 0, hi = nrow - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo + 1) / 2;
+        if (mid * ncol <= J)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    *y = lo;
+    *x = J - lo * ncol;
+    return 0;
+}
+
+/* Eq. (1) for every (x_i, y_j), i in [i0, i1), 0 <= j < ny:
+ * out[(i - i0) * ny + j] (row-major job order of Eq. (7)). */
+void oracle_cross_rows(const double *X, int64_t nx, int64_t ldx,
+                       const double *Y, int64_t ny, int64_t ldy, int64_t l,
+                       int64_t i0, int64_t i1, double *out)
+{
+    double *mx = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *sx = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *my = (double *)malloc(sizeof(double) * (size_t)ny);
+    double *sy = (double *)malloc(sizeof(double) * (size_t)ny);
+    oracle_row_stats(X, nx, l, ldx, mx, sx);
+    oracle_row_stats(Y, ny, l, ldy, my, sy);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = i0; i < i1; ++i) {
+        for (int64_t j = 0; j < ny; ++j) {
+            double num = centred_dot(X + i * ldx, mx[i], Y + j * ldy, my[j],
+                                     NULL, l);
+            out[oracle_cross_job_index(nx, ny, i, j) - i0 * ny] =
+                eq1(num, sx[i], sy[j]);
+        }
+    }
+    free(mx);
+    free(sx);
+    free(my);
+    free(sy);
+}
+
+/* Eq. (1) for a list of (x_{I[p]}, y_{Jc[p]}) */
+void oracle_cross_pairs(const double *X, int64_t nx, int64_t ldx,
+                        const double *Y, int64_t ny, int64_t ldy, int64_t l,
+                        int64_t npairs, const int64_t *I, const int64_t *Jc,
+                        double *r)
+{
+    double *mx = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *sx = (double *)malloc(sizeof(double) * (size_t)nx);
+    double *my = (double *)malloc(sizeof(double) * (size_t)ny);
+    double *sy = (double *)malloc(sizeof(double) * (size_t)ny);
+    oracle_row_stats(X, nx, l, ldx, mx, sx);
+    oracle_row_stats(Y, ny, l, ldy, my, sy);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < npairs; ++p) {
+        int64_t i = I[p], j = Jc[p];
+        double num = centred_dot(X + i * ldx, mx[i], Y + j * ldy, my[j],
+                                 NULL, l);
+        r[p] = eq1(num, sx[i], sy[j]);
+    }
+    free(mx);
+    free(sx);
+    free(my);
+    free(sy);
 }
 
 int oracle_num_threads(void)

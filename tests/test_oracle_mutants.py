@@ -46,6 +46,11 @@ MUTANTS = {
     "perm_count_strict": ("c += (rk >= robs);", "c += (rk > robs);"),
     "diag_row_count": ("return y * (2 * n - y + 1) / 2;",
                        "return y * (2 * n - y - 1) / 2;"),
+    "cross_index_column_major": ("return y * ncol + x;",
+                                 "return x * nrow + y;"),
+    "cross_wrong_stats": ("eq1(num, sx[i], sy[j]);\n        }",
+                          "eq1(num, sx[i], sx[j]);\n        }"),
+    "cross_search_strict": ("if (mid * ncol <= J)", "if (mid * ncol < J)"),
 }
 
 
@@ -144,6 +149,21 @@ def _pins(L):
     r2o, _ = _exact_r2(a, b)
     want = sum(_exact_r2(a, [b[s] for s in p])[0] >= r2o for p in allp)
     check("perm_complete", c[0] == want)
+    # non-symmetric jobs (Eq. (7)-(8)): numbering and the corrcoef block
+    ok = True
+    for nrow, ncol in ((5, 3), (3, 5)):
+        Jc = 0
+        for y in range(nrow):
+            for x in range(ncol):
+                ok &= oracle.cross_job_index(nrow, ncol, y, x, L) == Jc
+                ok &= oracle.cross_job_coords(nrow, ncol, Jc, L) == (y, x)
+                Jc += 1
+    check("cross_numbering", ok)
+    Xa = rng.standard_normal((11, 23)) * 2 + 1
+    Yb = rng.standard_normal((6, 23)) * 5 - 3
+    check("cross_corrcoef", np.max(np.abs(
+        oracle.cross_rows(Xa, Yb, L=L)
+        - np.corrcoef(np.vstack([Xa, Yb]))[:11, 11:])) <= 1e-14)
     return failed
 
 

@@ -357,3 +357,67 @@ def test_perm_band_counts_bracket():
     c, clo, chi = oracle.perm_counts(X, perms, I, J, delta=0.05)
     assert np.all(clo <= c) and np.all(c <= chi)
     assert np.any(clo < chi)
+
+
+# ------------------------------------------------- non-symmetric (cross)
+
+
+def test_cross_job_numbering_exhaustive():
+    # Eq. (7)-(8): row-major numbering of an nrow x ncol job matrix and its
+    # inverse, every job of several ragged shapes
+    for nrow, ncol in ((1, 1), (1, 7), (7, 1), (5, 3), (3, 5), (9, 13)):
+        J = 0
+        for y in range(nrow):
+            for x in range(ncol):
+                assert oracle.cross_job_index(nrow, ncol, y, x) == J
+                assert oracle.cross_job_coords(nrow, ncol, J) == (y, x)
+                J += 1
+        assert oracle.cross_job_index(nrow, ncol, nrow, 0) == -1
+        assert oracle.cross_job_index(nrow, ncol, 0, ncol) == -1
+        with pytest.raises(ValueError):
+            oracle.cross_job_coords(nrow, ncol, nrow * ncol)
+
+
+def test_cross_matches_corrcoef_block():
+    # the off-diagonal block of numpy.corrcoef over the stacked rows
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((11, 37)) * 3 + 5
+    Y = rng.standard_normal((6, 37)) - 2
+    R = oracle.cross_rows(X, Y)
+    C = np.corrcoef(np.vstack([X, Y]))[:11, 11:]
+    assert R.shape == (11, 6)
+    assert np.max(np.abs(R - C)) <= 1e-14
+
+
+def test_cross_closed_forms_and_bruteforce():
+    # r(x_i, a x_i + b) = sign(a) placed at known (i, j); exact rationals
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((4, 19))
+    Y = np.vstack([rng.standard_normal(19), -2.5 * X[2] + 1, 4 * X[0] - 3])
+    R = oracle.cross_rows(X, Y)
+    assert abs(R[2, 1] + 1) <= 1e-14 and abs(R[0, 2] - 1) <= 1e-14
+    for _ in range(15):
+        a = [int(t) for t in rng.integers(-9, 10, size=7)]
+        b = [int(t) for t in rng.integers(-9, 10, size=7)]
+        if len(set(a)) == 1 or len(set(b)) == 1:
+            continue
+        r2, sg = _exact_r2_sign(a, b)
+        got = oracle.cross_rows(np.array([a], float), np.array([b], float))
+        assert abs(got[0, 0] - sg * math.sqrt(float(r2))) <= 1e-15
+
+
+def test_cross_rows_slices_and_pairs_agree():
+    # rows [i0, i1) are the same numbers as the whole matrix's rows, and the
+    # pair list gives the same value at every (i, j); swapping X and Y
+    # transposes the result (Eq. (1) is symmetric in its operands)
+    rng = np.random.default_rng(23)
+    X = rng.random((9, 24))
+    Y = rng.random((14, 24))
+    R = oracle.cross_rows(X, Y)
+    assert np.array_equal(oracle.cross_rows(X, Y, 3, 7), R[3:7])
+    I, J = np.meshgrid(np.arange(9), np.arange(14), indexing="ij")
+    assert np.array_equal(oracle.cross_pairs(X, Y, I.ravel(), J.ravel()),
+                          R.ravel())
+    assert np.array_equal(oracle.cross_rows(Y, X), R.T)
+    assert np.array_equal(np.isnan(oracle.cross_rows(
+        np.vstack([X, np.full(24, 2.0)]), Y))[9], np.ones(14, bool))
