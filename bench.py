@@ -512,6 +512,61 @@ def run_batched(args):
     return 0
 
 
+def run_cross(args):
+    """Non-symmetric workload (Eq. (7)-(8)): r(x_i, y_j) between X = 65,536
+    x 512 and Y = 32,768 x 512 (log counts), dense FP32 R of 8.6 GB."""
+    import torch
+    import paper_1605_01584_gb300 as pcc
+    import synth
+    pcc.load()
+    nx, ny, l = 65536, 32768, 512
+    X = synth.counts_log(nx, l, 6)
+    Y = synth.counts_log(ny, l, 7)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.from_numpy(Y).cuda()
+    ZX = pcc.pcc_standardize(Xd, args.prec)
+    ZY = pcc.pcc_standardize(Yd, args.prec)
+    R = torch.empty((nx, ny), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pcc.pcc_standardize(Xd, args.prec, Z=ZX)
+        pcc.pcc_standardize(Yd, args.prec, Z=ZY)
+        pcc.pcc_cross_allpairs(ZX, ZY, R)
+
+    def kern():
+        pcc.pcc_cross_allpairs(ZX, ZY, R)
+
+    steps = max(3, min(args.steps, 20))
+    ms = _timed(step, steps, args.warmup, stream)
+    ms_k = _timed(kern, steps, 1, stream)
+    st = pcc.pcc_sync_status(ZX)
+    info = ZX.info()
+    tiles = pcc.pcc_cross_num_tiles(ZX, ZY)
+    nprod = 1 if info["prec"] == 4 else 3
+    exec_flops = nprod * 2 * 256 * 256 * info["lpad"] * tiles
+    out_bytes = nx * ny * 4 + 2 * 2 * (nx + ny) * info["lpad"]
+    hbm, bf16, bf16_sus, kind = peaks()
+    out = {"metric": "cross all-pairs Gpair*samples/s",
+           "value": nx * ny * l / (ms / 1e3) / 1e9,
+           "unit": "Gpair*samples/s", "ms_per_step": ms,
+           "ms_cross_kernel": ms_k, "steps": steps, "warmup": args.warmup,
+           "status": st, "dtype": {2: "bf16", 3: "f16", 4: "bf16"}.get(
+               info["prec"]),
+           "config": {"workload": "cross X 65536x512 vs Y 32768x512, dense "
+                      "FP32 R", "split": args.prec,
+                      "l2": "inputs and the 8.6 GB output exceed L2"},
+           "roofline": {"bound": "hbm", "achieved": out_bytes /
+                        (ms_k / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": out_bytes / (ms_k / 1e3) / 1e9 / hbm},
+           "roofline_split_executed": {
+               "bound": "tensor", "achieved": exec_flops / (ms_k / 1e3)
+               / 1e12, "peak": bf16_sus, "unit": "TFLOP/s",
+               "frac": exec_flops / (ms_k / 1e3) / 1e12 / bf16_sus}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,7 +576,7 @@ def main():
     ap.add_argument("--prec", default="auto",
                     choices=["auto", "bf16x3", "fp16x3s", "bf16x1"])
     ap.add_argument("--workload", default="allpairs",
-                    choices=["allpairs", "perm", "batched"])
+                    choices=["allpairs", "perm", "batched", "cross"])
     ap.add_argument("--n", type=int, default=N_GENES)
     ap.add_argument("--l", type=int, default=L_SAMPLES)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -537,6 +592,8 @@ def main():
         return run_perm(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "cross":
+        return run_cross(args)
     return run_gpu(args)
 
 

@@ -50,7 +50,8 @@ typedef enum {
     PCC_ERR_OOM = 3,         /* device allocation failed */
     PCC_ERR_CAPACITY = 4,    /* edge list longer than its capacity */
     PCC_ERR_TIMEOUT = 5,     /* a device pipeline wait exceeded its limit */
-    PCC_ERR_UNSUPPORTED = 6  /* no kernel for this device / combination */
+    PCC_ERR_UNSUPPORTED = 6, /* no kernel for this device / combination */
+    PCC_ERR_ABORTED = 7      /* a caller's callback asked to stop */
 } pcc_status;
 
 /* element type of an input or output array */
@@ -151,6 +152,78 @@ pcc_status pcc_allpairs_upper(const pcc_zmat *Z, void *R, pcc_dtype rt,
 pcc_status pcc_threshold_edges(const pcc_zmat *Z, float tau, pcc_edge *edges,
                                uint64_t capacity, uint64_t *d_count,
                                float *R, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Non-symmetric all pairs between two matrices (Section III-B,        */
+/* Eq. (7)-(8)): r(x_i, y_j) for every row x_i of X and y_j of Y.       */
+/* ------------------------------------------------------------------ */
+
+/* Number of work tiles of the cross schedule of ZX against ZY (the unit of
+ * tile ranges); -1 if either is NULL. */
+int64_t pcc_cross_num_tiles(const pcc_zmat *ZX, const pcc_zmat *ZY);
+
+/* Dense cross-correlation: R[i * ldr + j] = r(x_i, y_j) for 0 <= i < nx,
+ * 0 <= j < ny, over tiles [tile_begin, tile_end) of the cross schedule
+ * (tile_end = -1: all of them); other entries are not touched.
+ *   ZX, ZY  standardized by pcc_standardize on one device with the same l
+ *           and the same (resolved) form; ZX may equal ZY (the full square
+ *           matrix, diagonal included).
+ *   R       device, nx rows of ldr >= ny elements of type rt (PCC_F64 only
+ *           for PCC_PREC_FP64).  Flagged rows give NaN; tensor-core forms
+ *           clamp to [-1, 1].
+ * Errors: PCC_ERR_INVALID_ARG for NULL, mismatched Z's, ldr < ny, a bad
+ * range or dtype. */
+pcc_status pcc_cross_allpairs(const pcc_zmat *ZX, const pcc_zmat *ZY,
+                              void *R, pcc_dtype rt, int64_t ldr,
+                              int64_t tile_begin, int64_t tile_end,
+                              void *stream);
+
+/* Cross edges: every (i, j) with |r(x_i, y_j)| >= tau is appended as
+ * {i, j, r} (i indexes X, j indexes Y), with the same count and capacity
+ * rules as pcc_threshold_edges; R (FP32, pitch ldr, or NULL) is written in
+ * the same pass.  Not for PCC_PREC_FP64 with R. */
+pcc_status pcc_cross_edges(const pcc_zmat *ZX, const pcc_zmat *ZY, float tau,
+                           pcc_edge *edges, uint64_t capacity,
+                           uint64_t *d_count, float *R, int64_t ldr,
+                           void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Outputs larger than the device: passes with asynchronous copies     */
+/* (Section III-C's multi-pass execution, Algorithm 2).                 */
+/* ------------------------------------------------------------------ */
+
+/* Called on the calling thread once rows [row_begin, row_end) of the output
+ * are complete in host memory at `rows` (their packed slice, or for the
+ * cross form their dense rows), while the device computes the next pass.
+ * A non-zero return stops the computation (PCC_ERR_ABORTED). */
+typedef int32_t (*pcc_rows_sink)(void *user, int64_t row_begin,
+                                 int64_t row_end, const void *rows);
+
+/* The packed strict upper triangle of Z (as pcc_allpairs_upper) delivered
+ * to HOST memory in passes of whole row blocks, each computed into one of
+ * two device windows and copied out while the next pass computes.
+ *   R_host        host, n(n-1)/2 elements of type rt (pinned memory lets
+ *                 the copies overlap the kernels); NULL = no host copy of
+ *                 the whole triangle: each slice is staged in a
+ *                 library-owned pinned buffer, valid during the sink call.
+ *   device_bytes  bytes for the two windows (<= 0: a quarter of the free
+ *                 device memory, at most 4 GiB).
+ *   sink          may be NULL when R_host is given.
+ * Errors: PCC_ERR_INVALID_ARG (no R_host and no sink, bad dtype);
+ * PCC_ERR_OOM when one row block does not fit the budget;
+ * PCC_ERR_ABORTED.  Returns after the last slice was delivered; kernel
+ * status (timeouts) is read with pcc_sync_status. */
+pcc_status pcc_allpairs_upper_host(const pcc_zmat *Z, void *R_host,
+                                   pcc_dtype rt, int64_t device_bytes,
+                                   pcc_rows_sink sink, void *user,
+                                   void *stream);
+
+/* The same for the dense cross matrix: R_host rows of pitch ldr >= ny (a
+ * staged slice has pitch ny). */
+pcc_status pcc_cross_allpairs_host(const pcc_zmat *ZX, const pcc_zmat *ZY,
+                                   void *R_host, pcc_dtype rt, int64_t ldr,
+                                   int64_t device_bytes, pcc_rows_sink sink,
+                                   void *user, void *stream);
 
 /* Permutation test (Section IV-A): for permutations k in [k0, k1) of the P
  * given ones, r_k(i,j) = z_i . (z_j o pi_k) with (z_j o pi_k)[s] =

@@ -25,6 +25,7 @@ PCC_ERR_OOM = 3
 PCC_ERR_CAPACITY = 4
 PCC_ERR_TIMEOUT = 5
 PCC_ERR_UNSUPPORTED = 6
+PCC_ERR_ABORTED = 7
 # pcc_dtype
 PCC_F32 = 0
 PCC_F64 = 1
@@ -64,6 +65,10 @@ def header_functions() -> list[str]:
     return sorted(set(re.findall(r"\b(pcc_[a-z0-9_]+)\s*\(", txt)))
 
 
+_SINK = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_int64, ctypes.c_void_p)
+
+
 def load(path: str | None = None):
     """Load libpcc.so; raise if it has not been built."""
     global _lib
@@ -85,6 +90,14 @@ def load(path: str | None = None):
         "pcc_allpairs_upper": (_ST, [_P, _P, _I32, _I64, _I64, _P]),
         "pcc_threshold_edges": (_ST, [_P, ctypes.c_float, _P, _U64, _P, _P,
                                       _P]),
+        "pcc_cross_num_tiles": (_I64, [_P, _P]),
+        "pcc_cross_allpairs": (_ST, [_P, _P, _P, _I32, _I64, _I64, _I64, _P]),
+        "pcc_cross_edges": (_ST, [_P, _P, ctypes.c_float, _P, _U64, _P, _P,
+                                  _I64, _P]),
+        "pcc_allpairs_upper_host": (_ST, [_P, _P, _I32, _I64, _SINK, _P,
+                                          _P]),
+        "pcc_cross_allpairs_host": (_ST, [_P, _P, _P, _I32, _I64, _I64,
+                                          _SINK, _P, _P]),
         "pcc_perm_test": (_ST, [_P, _P, _I32, _I32, _I32, _P, _P]),
         "pcc_allpairs_upper_batched": (_ST, [_P, _I32, _P, _P]),
         "pcc_sync_status": (_ST, [_P, _P]),
@@ -208,6 +221,106 @@ def pcc_threshold_edges(Z: Zmat, tau: float, edges, capacity: int, d_count,
                                       int(capacity), _ptr(d_count), _ptr(R),
                                       _stream(stream)),
            "pcc_threshold_edges")
+
+
+def pcc_cross_num_tiles(ZX: Zmat, ZY: Zmat) -> int:
+    return int(load().pcc_cross_num_tiles(ZX.handle, ZY.handle))
+
+
+def pcc_cross_allpairs(ZX: Zmat, ZY: Zmat, R, ldr: int | None = None,
+                       tile_begin: int = 0, tile_end: int = -1, stream=None):
+    """R[i * ldr + j] = r(x_i, y_j) (Eq. (7)-(8)); R a device float32 (or
+    float64 for the FP64 form) buffer of nx rows of ldr (default ny)."""
+    import torch
+    rt = PCC_F64 if R.dtype == torch.float64 else PCC_F32
+    if ldr is None:
+        ldr = R.stride(0) if R.dim() == 2 else ZY.info()["n"]
+    _check(load().pcc_cross_allpairs(ZX.handle, ZY.handle, _ptr(R), rt,
+                                     int(ldr), tile_begin, tile_end,
+                                     _stream(stream)), "pcc_cross_allpairs")
+    return R
+
+
+def pcc_cross_edges(ZX: Zmat, ZY: Zmat, tau: float, edges, capacity: int,
+                    d_count, R=None, ldr: int | None = None, stream=None):
+    """Edges {i in X, j in Y, r} with |r| >= tau; optional dense FP32 R."""
+    if ldr is None:
+        ldr = (R.stride(0) if R is not None and R.dim() == 2
+               else ZY.info()["n"])
+    _check(load().pcc_cross_edges(ZX.handle, ZY.handle, float(tau),
+                                  _ptr(edges), int(capacity), _ptr(d_count),
+                                  _ptr(R), int(ldr), _stream(stream)),
+           "pcc_cross_edges")
+
+
+def _host_stream(call, n_rows_elems, esize, sink):
+    """Run a host-streaming entry point with a Python sink(r0, r1, view)."""
+    import numpy as np
+    err = []
+    cb = None
+    if sink is not None:
+        dt = np.float64 if esize == 8 else np.float32
+
+        def _cb(user, r0, r1, ptr):
+            try:
+                cnt = n_rows_elems(r0, r1)
+                buf = (ctypes.c_char * (cnt * esize)).from_address(ptr)
+                sink(r0, r1, np.frombuffer(buf, dtype=dt, count=cnt))
+                return 0
+            except BaseException as e:  # re-raised after the call returns
+                err.append(e)
+                return 1
+        cb = _SINK(_cb)
+    st = call(cb if cb is not None else _SINK())
+    if err:
+        raise err[0]
+    return st
+
+
+def pcc_allpairs_upper_host(Z: Zmat, R_host=None, device_bytes: int = 0,
+                            sink=None, stream=None):
+    """The packed triangle into host memory in overlapped passes; R_host a
+    numpy float32 array of n(n-1)/2 (float64 for the FP64 form) or None
+    with a sink(row_begin, row_end, slice) taking each packed slice."""
+    import numpy as np
+    info = Z.info()
+    n = info["n"]
+    f64 = R_host is not None and R_host.dtype == np.float64
+    rt = PCC_F64 if f64 else PCC_F32
+    if R_host is not None:
+        assert R_host.flags.c_contiguous and R_host.size == n * (n - 1) // 2
+
+    def elems(r0, r1):
+        return r1 * (2 * n - r1 - 1) // 2 - r0 * (2 * n - r0 - 1) // 2
+
+    hp = None if R_host is None else ctypes.c_void_p(R_host.ctypes.data)
+    st = _host_stream(
+        lambda cb: load().pcc_allpairs_upper_host(
+            Z.handle, hp, rt, int(device_bytes), cb, None, _stream(stream)),
+        elems, 8 if f64 else 4, sink)
+    _check(st, "pcc_allpairs_upper_host")
+    return R_host
+
+
+def pcc_cross_allpairs_host(ZX: Zmat, ZY: Zmat, R_host=None,
+                            device_bytes: int = 0, sink=None, stream=None):
+    """Dense cross matrix into host memory in overlapped passes; R_host a
+    2-D numpy array (nx x >= ny, unit inner stride) or None with a sink."""
+    import numpy as np
+    ny = ZY.info()["n"]
+    f64 = R_host is not None and R_host.dtype == np.float64
+    rt = PCC_F64 if f64 else PCC_F32
+    esize = 8 if f64 else 4
+    ldr = ny if R_host is None else R_host.strides[0] // esize
+    hp = None if R_host is None else ctypes.c_void_p(R_host.ctypes.data)
+    st = _host_stream(
+        lambda cb: load().pcc_cross_allpairs_host(
+            ZX.handle, ZY.handle, hp, rt, int(ldr), int(device_bytes), cb,
+            None, _stream(stream)),
+        lambda r0, r1: (r1 - r0) * ldr if R_host is not None
+        else (r1 - r0) * ny, esize, sink)
+    _check(st, "pcc_cross_allpairs_host")
+    return R_host
 
 
 def pcc_perm_test(Z: Zmat, d_perms, P: int, k0: int, k1: int, d_counts,

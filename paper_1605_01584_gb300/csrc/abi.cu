@@ -355,6 +355,83 @@ pcc_status pcc_threshold_edges(const pcc_zmat* Z, float tau, pcc_edge* edges,
                                        capacity, cnt, s));
 }
 
+int64_t pcc_cross_num_tiles(const pcc_zmat* ZX, const pcc_zmat* ZY) {
+  if (!ZX || !ZY) return -1;
+  if (is_split(ZX->prec)) return tc_cross_tiles(ZX->n, ZY->n);
+  return simt_cross_tiles(ZX, ZY);
+}
+
+namespace {
+// the two operands of a cross product must have been standardized alike
+bool cross_compatible(const pcc_zmat* ZX, const pcc_zmat* ZY) {
+  return ZX && ZY && ZX->device == ZY->device && ZX->l == ZY->l &&
+         ZX->lpad == ZY->lpad && ZX->prec == ZY->prec &&
+         ZX->scale_exp == ZY->scale_exp;
+}
+}  // namespace
+
+pcc_status pcc_cross_allpairs(const pcc_zmat* ZX, const pcc_zmat* ZY, void* R,
+                              pcc_dtype rt, int64_t ldr, int64_t tile_begin,
+                              int64_t tile_end, void* stream) {
+  if (!cross_compatible(ZX, ZY) || !R || ldr < ZY->n) return PCC_ERR_INVALID_ARG;
+  const int64_t T = pcc_cross_num_tiles(ZX, ZY);
+  if (tile_end < 0) tile_end = T;
+  if (tile_begin < 0 || tile_begin > tile_end || tile_end > T)
+    return PCC_ERR_INVALID_ARG;
+  if (rt != PCC_F32 && rt != PCC_F64) return PCC_ERR_INVALID_ARG;
+  if (rt == PCC_F64 && ZX->prec != PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (is_split(ZX->prec))
+    return cuda_status(launch_tc_cross(ZX, ZY, static_cast<float*>(R), ldr,
+                                       tile_begin, tile_end, false, 0.f,
+                                       nullptr, 0, nullptr, s));
+  return cuda_status(launch_simt_cross(ZX, ZY, R, rt, ldr, tile_begin,
+                                       tile_end, 0.f, nullptr, 0, nullptr, s));
+}
+
+pcc_status pcc_cross_edges(const pcc_zmat* ZX, const pcc_zmat* ZY, float tau,
+                           pcc_edge* edges, uint64_t capacity,
+                           uint64_t* d_count, float* R, int64_t ldr,
+                           void* stream) {
+  if (!cross_compatible(ZX, ZY) || !d_count || (capacity > 0 && !edges) ||
+      !(tau >= 0.f) || !isfinite(tau) || (R && ldr < ZY->n))
+    return PCC_ERR_INVALID_ARG;
+  if (R && ZX->prec == PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(d_count);
+  const int64_t T = pcc_cross_num_tiles(ZX, ZY);
+  if (is_split(ZX->prec))
+    return cuda_status(launch_tc_cross(ZX, ZY, R, ldr, 0, T, true, tau, edges,
+                                       capacity, cnt, s));
+  return cuda_status(launch_simt_cross(ZX, ZY, R, PCC_F32, ldr, 0, T, tau,
+                                       edges, capacity, cnt, s));
+}
+
+pcc_status pcc_allpairs_upper_host(const pcc_zmat* Z, void* R_host,
+                                   pcc_dtype rt, int64_t device_bytes,
+                                   pcc_rows_sink sink, void* user,
+                                   void* stream) {
+  if (!Z || (!R_host && !sink)) return PCC_ERR_INVALID_ARG;
+  if (rt != PCC_F32 && rt != PCC_F64) return PCC_ERR_INVALID_ARG;
+  if (rt == PCC_F64 && Z->prec != PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
+  return allpairs_host(Z, nullptr, R_host, rt, 0, device_bytes, sink, user,
+                       static_cast<cudaStream_t>(stream));
+}
+
+pcc_status pcc_cross_allpairs_host(const pcc_zmat* ZX, const pcc_zmat* ZY,
+                                   void* R_host, pcc_dtype rt, int64_t ldr,
+                                   int64_t device_bytes, pcc_rows_sink sink,
+                                   void* user, void* stream) {
+  if (!cross_compatible(ZX, ZY) || (!R_host && !sink) ||
+      (R_host && ldr < ZY->n))
+    return PCC_ERR_INVALID_ARG;
+  if (rt != PCC_F32 && rt != PCC_F64) return PCC_ERR_INVALID_ARG;
+  if (rt == PCC_F64 && ZX->prec != PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
+  return allpairs_host(ZX, ZY, R_host, rt, R_host ? ldr : ZY->n,
+                       device_bytes, sink, user,
+                       static_cast<cudaStream_t>(stream));
+}
+
 pcc_status pcc_perm_test(const pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                          int32_t k0, int32_t k1, uint32_t* d_counts,
                          void* stream) {
@@ -465,6 +542,7 @@ const char* pcc_status_string(pcc_status s) {
     case PCC_ERR_CAPACITY: return "edge list capacity exceeded";
     case PCC_ERR_TIMEOUT: return "device pipeline wait timed out";
     case PCC_ERR_UNSUPPORTED: return "unsupported device or combination";
+    case PCC_ERR_ABORTED: return "stopped by the caller's callback";
   }
   return "unknown status";
 }

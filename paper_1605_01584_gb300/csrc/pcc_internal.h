@@ -71,18 +71,44 @@ cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
 // K4/K5: CUDA-core pair kernels (FP32 / FP64 Z), tiles [t0, t1) of the
 // paper's triangular tile order.
 int simt_tile_size(pcc_prec p);
+// r_off: R holds the output from element r_off on (a window of rows).
 cudaError_t launch_simt_pairs(const pcc_zmat* Z, void* R, pcc_dtype rt,
                               int64_t t0, int64_t t1, float tau,
                               pcc_edge* edges, uint64_t cap,
-                              unsigned long long* count, cudaStream_t s);
+                              unsigned long long* count, cudaStream_t s,
+                              int64_t r_off = 0);
 
 // K2/K3: tensor-core pair kernel, tiles [t0, t1) of the banded super-tile
 // order (pcc_sched.h).
 int64_t tc_num_tiles(int64_t n);
+// G > 0 overrides the tuning's band rows (the tile numbering follows it).
 cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
                             int64_t t1, bool edges_on, float tau,
                             pcc_edge* edges, uint64_t cap,
-                            unsigned long long* count, cudaStream_t s);
+                            unsigned long long* count, cudaStream_t s,
+                            int64_t r_off = 0, int64_t G = 0);
+
+// Non-symmetric pairs between the rows of ZA and ZB (Eq. (7)-(8)), dense R
+// with row pitch ldr, tiles [t0, t1) of the cross schedule.
+int64_t tc_cross_tiles(int64_t na, int64_t nb);
+cudaError_t launch_tc_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, float* R,
+                            int64_t ldr, int64_t t0, int64_t t1,
+                            bool edges_on, float tau, pcc_edge* edges,
+                            uint64_t cap, unsigned long long* count,
+                            cudaStream_t s, int64_t r_off = 0,
+                            int64_t G = 0);
+int64_t simt_cross_tiles(const pcc_zmat* ZA, const pcc_zmat* ZB);
+cudaError_t launch_simt_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, void* R,
+                              pcc_dtype rt, int64_t ldr, int64_t t0,
+                              int64_t t1, float tau, pcc_edge* edges,
+                              uint64_t cap, unsigned long long* count,
+                              cudaStream_t s, int64_t r_off = 0);
+
+// Passes of whole row blocks into two device windows, copied to host memory
+// while the next pass computes (ZB = NULL: the packed triangle of ZA).
+pcc_status allpairs_host(const pcc_zmat* ZA, const pcc_zmat* ZB, void* host,
+                         pcc_dtype rt, int64_t ldh, int64_t device_bytes,
+                         pcc_rows_sink sink, void* user, cudaStream_t s);
 
 // K7: all pairs of B matrices in one persistent launch.
 pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,

@@ -11,6 +11,11 @@
 // here).  Instead of one thread per column (the Xeon Phi layout), 256
 // threads each own a TT x TT register block, K is staged through shared
 // memory BK at a time with a register prefetch of the next stage.
+//
+// CROSS: the non-symmetric job matrix between the rows of two matrices A
+// (n rows) and B (nb rows), Section III-B: tile t of the ma x mb tile grid
+// is numbered row-major, t = yt * mb + xt (Eq. (7)), and mapped back with
+// Eq. (8); every pair of a tile is valid and R is dense, R[i * ldr + j].
 #include <math.h>
 
 #include "pcc_internal.h"
@@ -55,14 +60,26 @@ __device__ __forceinline__ double vget<double2, double>(const double2& v,
   return q == 0 ? v.x : v.y;
 }
 
+struct SimtCross {
+  const void* Zb;          // B operand (== A for the triangle)
+  const uint8_t* flagsb;
+  int64_t nb;              // rows of B
+  int64_t mb;              // tile columns (CROSS)
+  int64_t ldr;             // row pitch of the dense R (CROSS)
+  int64_t r_off;           // R holds the output from element r_off on
+};
+
 template <typename T, typename OutT, int BT, int TT, int BK, bool WRITE_R,
-          bool EDGES>
+          bool EDGES, bool CROSS>
 __global__ void __launch_bounds__(256)
     k_pairs_simt(const T* __restrict__ Z, const uint8_t* __restrict__ flags,
                  int64_t n, int64_t lpad, int64_t m, int64_t t0,
                  OutT* __restrict__ R, float tau, pcc_edge* __restrict__ edges,
                  uint64_t cap, unsigned long long* __restrict__ count,
-                 int* __restrict__ status) {
+                 int* __restrict__ status, const SimtCross cx) {
+  const T* __restrict__ Zb = CROSS ? static_cast<const T*>(cx.Zb) : Z;
+  const uint8_t* __restrict__ flagsb = CROSS ? cx.flagsb : flags;
+  const int64_t nb = CROSS ? cx.nb : n;
   static_assert((BT / TT) * (BT / TT) == 256, "256 threads per tile");
   constexpr int H = TT / 2;
   constexpr int PAD = 4;
@@ -78,12 +95,18 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   int64_t yt, xt;
-  tri_coords(m, t0 + (int64_t)blockIdx.x, &yt, &xt);
+  if constexpr (CROSS) {
+    const int64_t t = t0 + (int64_t)blockIdx.x;
+    yt = t / cx.mb;  // Eq. (8)
+    xt = t - yt * cx.mb;
+  } else {
+    tri_coords(m, t0 + (int64_t)blockIdx.x, &yt, &xt);
+  }
   const int64_t row0 = yt * BT, col0 = xt * BT;
 
   if (tid < BT) {
     fr[tid] = (row0 + tid < n) ? flags[row0 + tid] : 1;
-    fc[tid] = (col0 + tid < n) ? flags[col0 + tid] : 1;
+    fc[tid] = (col0 + tid < nb) ? flagsb[col0 + tid] : 1;
   }
 
   V ra[NV], rb[NV];
@@ -99,8 +122,8 @@ __global__ void __launch_bounds__(256)
         za = *reinterpret_cast<const V*>(Z + (row0 + r) * lpad + k);
       else
         za = V{};
-      if (col0 + r < n)
-        zb = *reinterpret_cast<const V*>(Z + (col0 + r) * lpad + k);
+      if (col0 + r < nb)
+        zb = *reinterpret_cast<const V*>(Zb + (col0 + r) * lpad + k);
       else
         zb = V{};
       ra[v] = za;
@@ -164,12 +187,13 @@ __global__ void __launch_bounds__(256)
   for (int a = 0; a < TT; ++a) {
     const int li = a < H ? ty * H + a : BT / 2 + ty * H + (a - H);
     const int64_t i = row0 + li;
-    const int64_t base = pair_row_base(n, i);
+    const int64_t base =
+        (CROSS ? i * cx.ldr : pair_row_base(n, i)) - cx.r_off;
 #pragma unroll
     for (int b = 0; b < TT; ++b) {
       const int lj = b < H ? tx * H + b : BT / 2 + tx * H + (b - H);
       const int64_t j = col0 + lj;
-      const bool valid = (i < n) && (j < n) && (j > i);
+      const bool valid = (i < n) && (j < nb) && (CROSS || j > i);
       const bool flagged = (fr[li] | fc[lj]) != 0;
       T v = acc[a][b];
       v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
@@ -203,25 +227,51 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename T, typename OutT, int BT, int TT>
+template <typename T, typename OutT, int BT, int TT, bool CROSS>
 cudaError_t launch_t(const pcc_zmat* Z, OutT* R, int64_t t0, int64_t t1,
                      bool edges_on, float tau, pcc_edge* edges, uint64_t cap,
-                     unsigned long long* count, cudaStream_t s) {
+                     unsigned long long* count, cudaStream_t s,
+                     const SimtCross& cx) {
   const int64_t m = (Z->n + BT - 1) / BT;
   const int64_t nblocks = t1 - t0;
   if (nblocks <= 0) return cudaSuccess;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const T* z = reinterpret_cast<const T*>(Z->z);
   if (edges_on && R)
-    k_pairs_simt<T, OutT, BT, TT, 16, true, true><<<(unsigned)nblocks, 256, 0, s>>>(
-        z, Z->flags, Z->n, Z->lpad, m, t0, R, tau, edges, cap, count, Z->status);
+    k_pairs_simt<T, OutT, BT, TT, 16, true, true, CROSS>
+        <<<(unsigned)nblocks, 256, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
+                                           R, tau, edges, cap, count,
+                                           Z->status, cx);
   else if (edges_on)
-    k_pairs_simt<T, OutT, BT, TT, 16, false, true><<<(unsigned)nblocks, 256, 0, s>>>(
-        z, Z->flags, Z->n, Z->lpad, m, t0, R, tau, edges, cap, count, Z->status);
+    k_pairs_simt<T, OutT, BT, TT, 16, false, true, CROSS>
+        <<<(unsigned)nblocks, 256, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
+                                           R, tau, edges, cap, count,
+                                           Z->status, cx);
   else
-    k_pairs_simt<T, OutT, BT, TT, 16, true, false><<<(unsigned)nblocks, 256, 0, s>>>(
-        z, Z->flags, Z->n, Z->lpad, m, t0, R, tau, edges, cap, count, Z->status);
+    k_pairs_simt<T, OutT, BT, TT, 16, true, false, CROSS>
+        <<<(unsigned)nblocks, 256, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
+                                           R, tau, edges, cap, count,
+                                           Z->status, cx);
   return cudaGetLastError();
+}
+
+template <bool CROSS>
+cudaError_t launch_prec(const pcc_zmat* Z, void* R, pcc_dtype rt, int64_t t0,
+                        int64_t t1, float tau, pcc_edge* edges, uint64_t cap,
+                        unsigned long long* count, cudaStream_t s,
+                        const SimtCross& cx) {
+  const bool edges_on = count != nullptr;
+  if (Z->prec == PCC_PREC_FP32)
+    return launch_t<float, float, 128, 8, CROSS>(
+        Z, reinterpret_cast<float*>(R), t0, t1, edges_on, tau, edges, cap,
+        count, s, cx);
+  if (rt == PCC_F64)
+    return launch_t<double, double, 64, 4, CROSS>(
+        Z, reinterpret_cast<double*>(R), t0, t1, edges_on, tau, edges, cap,
+        count, s, cx);
+  return launch_t<double, float, 64, 4, CROSS>(Z, reinterpret_cast<float*>(R),
+                                               t0, t1, edges_on, tau, edges,
+                                               cap, count, s, cx);
 }
 
 }  // namespace
@@ -231,19 +281,26 @@ int simt_tile_size(pcc_prec p) { return p == PCC_PREC_FP64 ? 64 : 128; }
 cudaError_t launch_simt_pairs(const pcc_zmat* Z, void* R, pcc_dtype rt,
                               int64_t t0, int64_t t1, float tau,
                               pcc_edge* edges, uint64_t cap,
-                              unsigned long long* count, cudaStream_t s) {
-  const bool edges_on = count != nullptr;
-  if (Z->prec == PCC_PREC_FP32)
-    return launch_t<float, float, 128, 8>(Z, reinterpret_cast<float*>(R), t0,
-                                          t1, edges_on, tau, edges, cap,
-                                          count, s);
-  if (rt == PCC_F64)
-    return launch_t<double, double, 64, 4>(Z, reinterpret_cast<double*>(R),
-                                           t0, t1, edges_on, tau, edges, cap,
-                                           count, s);
-  return launch_t<double, float, 64, 4>(Z, reinterpret_cast<float*>(R), t0,
-                                        t1, edges_on, tau, edges, cap, count,
-                                        s);
+                              unsigned long long* count, cudaStream_t s,
+                              int64_t r_off) {
+  const SimtCross cx{Z->z, Z->flags, Z->n, 0, 0, r_off};
+  return launch_prec<false>(Z, R, rt, t0, t1, tau, edges, cap, count, s, cx);
+}
+
+int64_t simt_cross_tiles(const pcc_zmat* ZA, const pcc_zmat* ZB) {
+  const int64_t t = simt_tile_size(ZA->prec);
+  return ((ZA->n + t - 1) / t) * ((ZB->n + t - 1) / t);
+}
+
+cudaError_t launch_simt_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, void* R,
+                              pcc_dtype rt, int64_t ldr, int64_t t0,
+                              int64_t t1, float tau, pcc_edge* edges,
+                              uint64_t cap, unsigned long long* count,
+                              cudaStream_t s, int64_t r_off) {
+  const int64_t t = simt_tile_size(ZA->prec);
+  const SimtCross cx{ZB->z, ZB->flags, ZB->n, (ZB->n + t - 1) / t, ldr,
+                     r_off};
+  return launch_prec<true>(ZA, R, rt, t0, t1, tau, edges, cap, count, s, cx);
 }
 
 }  // namespace pcc

@@ -10,6 +10,10 @@
 // unflagged take a branch-free path, and the (rare) edge append rescans a
 // block only when some |r| >= tau.
 //
+// DENSE: the non-symmetric form (rows of one matrix against the rows of
+// another): every (i < n, j < ncol) is a pair, and row i of R starts at
+// base0 + (i - rbase) * ldr.
+//
 // Why two accumulators for long rows: the tensor cores' FP32 accumulation
 // rounds every update toward zero, so its error grows with the number of
 // updates into a large partial sum (measured: 1.2e-5 on |r| ~ 1 at l = 2048
@@ -41,18 +45,22 @@ struct EpiOut {
 // blocks) and t_row2 addresses the second, summed here in FP32; stg: this
 // warp's 32 x kStagePad floats; rbase: first row; jw0: first column; base0 =
 // pair_row_base(n, rbase); rflags: bit rr = row rbase+rr flagged (or >= n);
-// cfl[c]: flag of column jw0 + 32c + lane.
-template <bool WRITE_R, bool EDGES, bool DUAL = false>
+// cfl[c]: flag of column jw0 + 32c + lane; ncol, ldr: DENSE only.
+template <bool WRITE_R, bool EDGES, bool DUAL = false, bool DENSE = false>
 __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
                                               int lane, int64_t n,
                                               int64_t rbase, int64_t jw0,
                                               int64_t base0, uint32_t rflags,
                                               const int (&cfl)[4],
                                               const EpiOut& eo,
-                                              uint32_t t_row2 = 0) {
-  // warp-uniform: does 32 x 32 block c hold any pair i < j < n?
+                                              uint32_t t_row2 = 0,
+                                              int64_t ncol = 0,
+                                              int64_t ldr = 0) {
+  if constexpr (!DENSE) ncol = n;
+  // warp-uniform: does 32 x 32 block c hold any pair?
   auto active = [&](int c) {
     const int64_t jc0 = jw0 + c * 32;
+    if constexpr (DENSE) return !(rbase >= n || jc0 >= ncol);
     return !(rbase >= n || jc0 >= n || jc0 + 31 <= rbase);
   };
   auto next_active = [&](int c) {
@@ -86,11 +94,13 @@ __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
     const int64_t jc0 = jw0 + c * 32;
     const int64_t j = jc0 + lane;
     const bool cflag = cfl[c] != 0;
-    const bool clean = (jc0 > rbase + 31) && (jc0 + 31 < n) &&
+    const bool clean = (DENSE || jc0 > rbase + 31) && (jc0 + 31 < ncol) &&
                        (rbase + 31 < n) && rflags == 0 &&
                        !__any_sync(0xffffffffu, cflag);
     float* out = eo.R + base0 + j;
-    int64_t step = n - rbase - 2;
+    // packed rows: row i+1 starts n - i - 2 after row i; dense rows: ldr
+    int64_t step = DENSE ? ldr : n - rbase - 2;
+    constexpr int64_t kDec = DENSE ? 0 : 1;
     bool hit = false;
     if (clean) {
       // every pair of the block is valid and unflagged
@@ -101,7 +111,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
         if constexpr (WRITE_R) __stcs(out, r);
         if constexpr (EDGES) hit |= fabsf(r) >= eo.tau;
         out += step;
-        --step;
+        step -= kDec;
       }
     } else {
       hit = true;  // edges (if any) are handled by the scan below
@@ -112,9 +122,9 @@ __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
           float r = stg[rr * kStagePad + lane] * eo.scale;
           r = fminf(1.f, fmaxf(-1.f, r));
           if (((rflags >> rr) & 1u) || cflag) r = __int_as_float(0x7fc00000);
-          if (i < n && j < n && j > i) __stcs(out, r);
+          if (i < n && j < ncol && (DENSE || j > i)) __stcs(out, r);
           out += step;
-          --step;
+          step -= kDec;
         }
       }
     }
@@ -127,7 +137,8 @@ __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
           float r = stg[rr * kStagePad + lane] * eo.scale;
           r = fminf(1.f, fmaxf(-1.f, r));
           const bool fl = ((rflags >> rr) & 1u) || cflag;
-          const bool e = i < n && j < n && j > i && !fl && fabsf(r) >= eo.tau;
+          const bool e = i < n && j < ncol && (DENSE || j > i) && !fl &&
+                         fabsf(r) >= eo.tau;
           const unsigned mask = __ballot_sync(0xffffffffu, e);
           if (mask) {
             const int leader = __ffs(mask) - 1;

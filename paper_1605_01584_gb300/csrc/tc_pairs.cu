@@ -30,7 +30,15 @@
 //               contiguous), clamp to [-1,1], NaN for flagged rows, and the
 //               optional warp-aggregated edge append.
 // The two accumulators let the epilogue of one unit overlap the MMAs of the
-// next.  By default the grid is made of 2-CTA clusters: the CTAs of a pair
+// next.
+//
+// CROSS: the non-symmetric job matrix between the rows of two matrices
+// (Section III-B, Eq. (7)-(8)): A rows come from the first, B rows from the
+// second, every super-tile of the my x mx grid is computed, and the
+// epilogue writes a dense row-major R (pitch ldr).  Super-tiles are taken
+// in bands of G rows, column by column within a band (Eq. (7)-(8) with the
+// roles of rows and columns swapped, per band), so that a band's A rows
+// stay in L2 while B streams past them once.  By default the grid is made of 2-CTA clusters: the CTAs of a pair
 // compute the two halves of one super-tile, which need the same 256 B rows,
 // so each loads 128 of them and multicasts them to both (a third less L2 to
 // shared-memory traffic); both MMAs must release a stage before either
@@ -57,8 +65,14 @@ constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 
 struct TcParams {
-  int64_t n;
-  int64_t m;         // super-tiles per side
+  int64_t n;         // rows (of the first matrix)
+  int64_t m;         // super-tiles per side (CROSS: super-tile rows)
+  int64_t ncol;      // columns: n, or the second matrix's rows (CROSS)
+  int64_t mcol;      // CROSS: super-tile columns
+  int64_t ldr;       // CROSS: row pitch of R
+  int64_t r_off;     // R holds the output from element r_off on (a window
+                     // of whole rows, for passes that do not fit at once)
+  const uint8_t* cflags;  // flags of the column variables
   int64_t G;         // super-tile rows per band (pcc_sched.h)
   int64_t u_begin;   // units [u_begin, u_end)
   int64_t u_end;
@@ -96,19 +110,36 @@ struct Cfg {
   static_assert(kSmemBytes <= 232448, "shared memory budget");
 };
 
+template <bool CROSS>
 __device__ __forceinline__ void unit_coords(BandCursor* cur, const TcParams& p,
                                             int64_t u, int64_t* row0,
                                             int64_t* col0) {
   int64_t yt, xt;
-  band_tile_coords(cur, p.m, p.G, u >> 1, &yt, &xt);
+  if constexpr (CROSS) {
+    const int64_t t = u >> 1;
+    const int64_t per_band = p.G * p.mcol;
+    const int64_t b = t / per_band;
+    const int64_t tb = t - b * per_band;
+    const int64_t rows = p.m - b * p.G < p.G ? p.m - b * p.G : p.G;
+    xt = tb / rows;
+    yt = b * p.G + (tb - xt * rows);
+  } else {
+    band_tile_coords(cur, p.m, p.G, u >> 1, &yt, &xt);
+  }
   *row0 = yt * kTcSuper + (u & 1) * kBM;
   *col0 = xt * kTcSuper;
 }
 
-template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, int CL>
+template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, int CL,
+          bool CROSS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap tm_hi,
-               const __grid_constant__ CUtensorMap tm_lo, const TcParams p) {
+               const __grid_constant__ CUtensorMap tm_lo,
+               const __grid_constant__ CUtensorMap tmb_hi,
+               const __grid_constant__ CUtensorMap tmb_lo, const TcParams p) {
+  // B operand maps: the second matrix's for CROSS, else Z's own
+  const CUtensorMap* mb_hi = CROSS ? &tmb_hi : &tm_hi;
+  const CUtensorMap* mb_lo = CROSS ? &tmb_lo : &tm_lo;
   using C = Cfg<NPROD, KB>;
   constexpr int kTileA = C::kTileA;
   constexpr int kTileB = C::kTileB;
@@ -158,6 +189,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0 && lane == 0) {
     tma_prefetch_desc(&tm_hi);
     if (NPROD > 1) tma_prefetch_desc(&tm_lo);
+    if (CROSS) {
+      tma_prefetch_desc(&tmb_hi);
+      if (NPROD > 1) tma_prefetch_desc(&tmb_lo);
+    }
   }
   if (warp == 1) {
     tmem_alloc(tmem_holder, 512);
@@ -188,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end && !p.drop_loads;
            u += gridDim.x) {
         int64_t row0, col0;
-        unit_coords(&cur, p, u, &row0, &col0);
+        unit_coords<CROSS>(&cur, p, u, &row0, &col0);
         // a cluster's CTAs run their units in lockstep (they share B), so
         // only the single-CTA form skips units below the last row
         if (CL == 1 && row0 >= n) continue;
@@ -205,14 +240,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           tma_load_2d_hint(sA_hi(stage), &tm_hi, &full[stage], kc, (int)row0,
                            pol);
           if constexpr (CL == 1) {
-            tma_load_2d_hint(sB_hi(stage), &tm_hi, &full[stage], kc,
+            tma_load_2d_hint(sB_hi(stage), mb_hi, &full[stage], kc,
                              (int)col0, pol);
-            tma_load_2d_hint(sB_hi(stage) + kTileA, &tm_hi, &full[stage], kc,
+            tma_load_2d_hint(sB_hi(stage) + kTileA, mb_hi, &full[stage], kc,
                              (int)col0 + kBM, pol);
           } else {
             // both CTAs need all 256 B rows: each loads its 128 and
             // multicasts them to the pair
-            tma_load_2d_mc(sB_hi(stage) + crank * kTileA, &tm_hi,
+            tma_load_2d_mc(sB_hi(stage) + crank * kTileA, mb_hi,
                            &full[stage], kc, (int)(col0 + crank * kBM), 3,
                            pol);
           }
@@ -220,12 +255,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d_hint(sA_lo(stage), &tm_lo, &full[stage], kc,
                              (int)row0, pol);
             if constexpr (CL == 1) {
-              tma_load_2d_hint(sB_lo(stage), &tm_lo, &full[stage], kc,
+              tma_load_2d_hint(sB_lo(stage), mb_lo, &full[stage], kc,
                                (int)col0, pol);
-              tma_load_2d_hint(sB_lo(stage) + kTileA, &tm_lo, &full[stage],
+              tma_load_2d_hint(sB_lo(stage) + kTileA, mb_lo, &full[stage],
                                kc, (int)col0 + kBM, pol);
             } else {
-              tma_load_2d_mc(sB_lo(stage) + crank * kTileA, &tm_lo,
+              tma_load_2d_mc(sB_lo(stage) + crank * kTileA, mb_lo,
                              &full[stage], kc, (int)(col0 + crank * kBM), 3,
                              pol);
             }
@@ -257,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t aphase = 0;
       for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
         int64_t row0, col0;
-        unit_coords(&cur, p, u, &row0, &col0);
+        unit_coords<CROSS>(&cur, p, u, &row0, &col0);
         if (CL == 1 && row0 >= n) continue;
         if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
         const int acc0 = acc;
@@ -331,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t aphase = 0;
     for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
       int64_t row0, col0;
-      unit_coords(&cur, p, u, &row0, &col0);
+      unit_coords<CROSS>(&cur, p, u, &row0, &col0);
       if (CL == 1 && row0 >= n) continue;
       const int64_t rbase = row0 + q * 32;  // first row of this warp
       const int64_t jw0 = col0 + h * 128;   // first column of this warp
@@ -342,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int64_t jj = jw0 + c * 32 + lane;
-        cfl[c] = (jj < n) ? p.flags[jj] : 1;
+        cfl[c] = (jj < p.ncol) ? p.cflags[jj] : 1;
       }
       bool ok = true;
       const int acc0 = acc;
@@ -355,19 +390,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
       tc_fence_after();
       const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
-      // packed index of (rbase, 0); row i+1 starts n - i - 2 later
-      const int64_t base0 = pair_row_base(n, rbase);
+      // packed index of (rbase, 0); row i+1 starts n - i - 2 later (dense:
+      // rbase * ldr, rows ldr apart)
+      const int64_t base0 =
+          (CROSS ? rbase * p.ldr : pair_row_base(n, rbase)) - p.r_off;
       const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
       const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
       const EpiOut eo{p.R, p.out_scale, p.tau, p.edges, p.count, p.cap,
                       p.status};
       if (p.kalt)
-        epilogue_rows<WRITE_R, EDGES, true>(
+        epilogue_rows<WRITE_R, EDGES, true, CROSS>(
             t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo,
-            tmem_base + lane_off + (uint32_t)(acc * kBN));
+            tmem_base + lane_off + (uint32_t)(acc * kBN), p.ncol, p.ldr);
       else
-        epilogue_rows<WRITE_R, EDGES>(t_row, stg, lane, n, rbase, jw0, base0,
-                                      rflags, cfl, eo);
+        epilogue_rows<WRITE_R, EDGES, false, CROSS>(
+            t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo, 0,
+            p.ncol, p.ldr);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
@@ -390,15 +428,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB>
-cudaError_t launch_inst(const pcc_zmat* Z, const TcParams& p, int grid,
-                        cudaStream_t s) {
+template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, bool CROSS>
+cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
+                        const TcParams& p, int grid, cudaStream_t s) {
   const int smem = Cfg<NPROD, KB>::kSmemBytes;
   const CUtensorMap& th = KB == 64 ? Z->tm_hi : Z->tm_hi32;
   const CUtensorMap& tl = KB == 64 ? Z->tm_lo : Z->tm_lo32;
+  const CUtensorMap& tbh = KB == 64 ? ZB->tm_hi : ZB->tm_hi32;
+  const CUtensorMap& tbl = KB == 64 ? ZB->tm_lo : ZB->tm_lo32;
   const int64_t tiles = (p.u_end - p.u_begin) / 2;
   if (tc_tuning().cluster == 2 && tiles >= 2) {
-    auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2>;
+    auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2, CROSS>;
     cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -425,41 +465,72 @@ cudaError_t launch_inst(const pcc_zmat* Z, const TcParams& p, int grid,
     }
     int64_t ncl = tiles < max_clusters ? tiles : max_clusters;
     cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
-    e = cudaLaunchKernelEx(&cfg, fn, th, tl, p);
+    e = cudaLaunchKernelEx(&cfg, fn, th, tl, tbh, tbl, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 1>;
+  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 1, CROSS>;
   cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, kThreads, smem, s>>>(th, tl, p);
+  fn<<<grid, kThreads, smem, s>>>(th, tl, tbh, tbl, p);
   return cudaGetLastError();
 }
 
-template <int NPROD, bool BF16, int KB>
-cudaError_t launch_prec(const pcc_zmat* Z, const TcParams& p, int grid,
-                        bool write_r, bool edges_on, cudaStream_t s) {
+template <int NPROD, bool BF16, int KB, bool CROSS>
+cudaError_t launch_prec(const pcc_zmat* Z, const pcc_zmat* ZB,
+                        const TcParams& p, int grid, bool write_r,
+                        bool edges_on, cudaStream_t s) {
   if (write_r && edges_on)
-    return launch_inst<NPROD, BF16, true, true, KB>(Z, p, grid, s);
-  if (edges_on) return launch_inst<NPROD, BF16, false, true, KB>(Z, p, grid, s);
-  return launch_inst<NPROD, BF16, true, false, KB>(Z, p, grid, s);
+    return launch_inst<NPROD, BF16, true, true, KB, CROSS>(Z, ZB, p, grid, s);
+  if (edges_on)
+    return launch_inst<NPROD, BF16, false, true, KB, CROSS>(Z, ZB, p, grid,
+                                                            s);
+  return launch_inst<NPROD, BF16, true, false, KB, CROSS>(Z, ZB, p, grid, s);
 }
 
-template <int KB>
-cudaError_t launch_kb(const pcc_zmat* Z, TcParams& p, int grid, bool write_r,
-                      bool edges_on, cudaStream_t s) {
+template <int KB, bool CROSS>
+cudaError_t launch_kb(const pcc_zmat* Z, const pcc_zmat* ZB, TcParams& p,
+                      int grid, bool write_r, bool edges_on, cudaStream_t s) {
   p.nkb = (int)(Z->lpad / KB);
   p.kalt = (Z->lpad > kKaltMinL && p.nkb >= 2) ? 1 : 0;
   switch (Z->prec) {
     case PCC_PREC_BF16X3:
-      return launch_prec<3, true, KB>(Z, p, grid, write_r, edges_on, s);
+      return launch_prec<3, true, KB, CROSS>(Z, ZB, p, grid, write_r,
+                                             edges_on, s);
     case PCC_PREC_FP16X3S:
-      return launch_prec<3, false, KB>(Z, p, grid, write_r, edges_on, s);
+      return launch_prec<3, false, KB, CROSS>(Z, ZB, p, grid, write_r,
+                                              edges_on, s);
     case PCC_PREC_BF16X1:
-      return launch_prec<1, true, KB>(Z, p, grid, write_r, edges_on, s);
+      return launch_prec<1, true, KB, CROSS>(Z, ZB, p, grid, write_r,
+                                             edges_on, s);
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+TcParams base_params(const pcc_zmat* Z, float* R, float tau,
+                     pcc_edge* edges, uint64_t cap,
+                     unsigned long long* count) {
+  TcParams p;
+  p.n = Z->n;
+  p.m = tc_super_count(Z->n);
+  p.ncol = Z->n;
+  p.mcol = 0;
+  p.ldr = 0;
+  p.r_off = 0;
+  p.cflags = Z->flags;
+  p.G = tc_tuning().band;
+  p.out_scale = (float)ldexp(1.0, -2 * Z->scale_exp);
+  p.tau = tau;
+  p.flags = Z->flags;
+  p.R = R;
+  p.edges = edges;
+  p.count = count;
+  p.cap = cap;
+  p.status = Z->status;
+  p.wait_ns = wait_limit_ns();
+  p.drop_loads = debug_drop_loads() ? 1 : 0;
+  return p;
 }
 
 }  // namespace
@@ -472,31 +543,46 @@ int64_t tc_num_tiles(int64_t n) {
 cudaError_t launch_tc_pairs(const pcc_zmat* Z, float* R, int64_t t0,
                             int64_t t1, bool edges_on, float tau,
                             pcc_edge* edges, uint64_t cap,
-                            unsigned long long* count, cudaStream_t s) {
+                            unsigned long long* count, cudaStream_t s,
+                            int64_t r_off, int64_t G) {
   if (t1 <= t0) return cudaSuccess;
-  TcParams p;
-  p.n = Z->n;
-  p.m = tc_super_count(Z->n);
-  p.G = tc_tuning().band;
+  TcParams p = base_params(Z, R, tau, edges, cap, count);
+  p.r_off = r_off;
+  if (G > 0) p.G = G;
   p.u_begin = 2 * t0;
   p.u_end = 2 * t1;
-  p.out_scale = (float)ldexp(1.0, -2 * Z->scale_exp);
-  p.tau = tau;
-  p.flags = Z->flags;
-  p.R = R;
-  p.edges = edges;
-  p.count = count;
-  p.cap = cap;
-  p.status = Z->status;
-  p.wait_ns = wait_limit_ns();
-  p.drop_loads = debug_drop_loads() ? 1 : 0;
   const int64_t units = p.u_end - p.u_begin;
   int grid = num_sms(Z->device);
   if (units < grid) grid = (int)units;
   const bool write_r = R != nullptr;
   if (tc_tuning().stage_k == 64)
-    return launch_kb<64>(Z, p, grid, write_r, edges_on, s);
-  return launch_kb<32>(Z, p, grid, write_r, edges_on, s);
+    return launch_kb<64, false>(Z, Z, p, grid, write_r, edges_on, s);
+  return launch_kb<32, false>(Z, Z, p, grid, write_r, edges_on, s);
+}
+
+int64_t tc_cross_tiles(int64_t na, int64_t nb) {
+  return tc_super_count(na) * tc_super_count(nb);
+}
+
+cudaError_t launch_tc_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, float* R,
+                            int64_t ldr, int64_t t0, int64_t t1,
+                            bool edges_on, float tau, pcc_edge* edges,
+                            uint64_t cap, unsigned long long* count,
+                            cudaStream_t s, int64_t r_off, int64_t G) {
+  if (t1 <= t0) return cudaSuccess;
+  TcParams p = base_params(ZA, R, tau, edges, cap, count);
+  p.r_off = r_off;
+  if (G > 0) p.G = G;
+  p.ncol = ZB->n;
+  p.mcol = tc_super_count(ZB->n);
+  p.ldr = ldr;
+  p.cflags = ZB->flags;
+  p.u_begin = 2 * t0;
+  p.u_end = 2 * t1;
+  const int64_t units = p.u_end - p.u_begin;
+  int grid = num_sms(ZA->device);
+  if (units < grid) grid = (int)units;
+  return launch_kb<32, true>(ZA, ZB, p, grid, R != nullptr, edges_on, s);
 }
 
 }  // namespace pcc
