@@ -513,13 +513,14 @@ def run_batched(args):
 
 
 def run_cross(args):
-    """Non-symmetric workload (Eq. (7)-(8)): r(x_i, y_j) between X = 65,536
-    x 512 and Y = 32,768 x 512 (log counts), dense FP32 R of 8.6 GB."""
+    """Non-symmetric workload (Eq. (7)-(8)): r(x_i, y_j) between X = n x l
+    and Y = n/2 x l (log counts; default 65,536 and 32,768 x 512), dense
+    FP32 R (8.6 GB at the default)."""
     import torch
     import paper_1605_01584_gb300 as pcc
     import synth
     pcc.load()
-    nx, ny, l = 65536, 32768, 512
+    nx, ny, l = args.n, args.n // 2, args.l
     X = synth.counts_log(nx, l, 6)
     Y = synth.counts_log(ny, l, 7)
     Xd = torch.from_numpy(X).cuda()
@@ -553,7 +554,7 @@ def run_cross(args):
            "ms_cross_kernel": ms_k, "steps": steps, "warmup": args.warmup,
            "status": st, "dtype": {2: "bf16", 3: "f16", 4: "bf16"}.get(
                info["prec"]),
-           "config": {"workload": "cross X 65536x512 vs Y 32768x512, dense "
+           "config": {"workload": f"cross X {nx}x{l} vs Y {ny}x{l}, dense "
                       "FP32 R", "split": args.prec,
                       "l2": "inputs and the 8.6 GB output exceed L2"},
            "roofline": {"bound": "hbm", "achieved": out_bytes /
@@ -567,6 +568,74 @@ def run_cross(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's own shapes, as context (Section IV): U[0,1] with n = 16K,
+    32K, 64K and l = 5,000, and a 17,555 x 5,072 log-count stand-in for the
+    human dataset; each in FP64 on CUDA cores (the paper's precision) and in
+    the default split form on tensor cores, one full triangle per run, with
+    max|dr| over 20,000 sampled pairs against the oracle.  The paper's
+    one-Phi times are quoted beside them."""
+    import torch
+    import oracle
+    import paper_1605_01584_gb300 as pcc
+    import synth
+    pcc.load()
+    shapes = [("uniform 16K x 5K", 16000, 5000, 27.4),
+              ("uniform 32K x 5K", 32000, 5000, 83.2),
+              ("uniform 64K x 5K", 64000, 5000, 285.4),
+              ("counts 17,555 x 5,072 (human stand-in)", 17555, 5072, 32.1)]
+    runs = []
+    for name, n, l, phi_s in shapes:
+        if n > args.n:
+            continue
+        if name.startswith("uniform"):
+            X = synth.uniform01(n, l, 8)
+        else:
+            X = synth.counts_log(n, l, 9)
+        Xd = torch.from_numpy(X).cuda()
+        rng = np.random.default_rng(10)
+        I = rng.integers(0, n - 1, 20000)
+        J = np.minimum(I + 1 + rng.integers(0, n, 20000) % (n - 1 - I), n - 1)
+        want = oracle.pcc_pairs(X, I, J)
+        idx = torch.from_numpy(I * (2 * n - I - 1) // 2 + (J - I - 1)).cuda()
+        for prec in ("fp64", args.prec):
+            dt = torch.float64 if prec == "fp64" else torch.float32
+            R = torch.empty(n * (n - 1) // 2, dtype=dt, device="cuda")
+            Z = pcc.pcc_standardize(Xd, prec)
+
+            def step():
+                pcc.pcc_standardize(Xd, prec, Z=Z)
+                pcc.pcc_allpairs_upper(Z, R)
+
+            step()
+            torch.cuda.synchronize()
+            reps = 1 if prec == "fp64" else 3
+            ms = _timed(step, reps, 0, torch.cuda.current_stream())
+            st = pcc.pcc_sync_status(Z)
+            got = R[idx].double().cpu().numpy()
+            ok = ~np.isnan(want)
+            err = float(np.max(np.abs(got[ok] - want[ok])))
+            info = Z.info()
+            runs.append({"data": name, "n": n, "l": l,
+                         "form": {0: "fp64", 1: "fp32", 2: "bf16x3",
+                                  3: "fp16x3s", 4: "bf16x1"}[info["prec"]],
+                         "seconds": ms / 1e3, "status": st,
+                         "max_abs_dr_sampled": err,
+                         "Gpair_samples_per_s": n * (n - 1) / 2 * l
+                         / (ms / 1e3) / 1e9,
+                         "paper_one_phi_fp64_seconds": phi_s})
+            print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
+            del R, Z
+            torch.cuda.empty_cache()
+    out = {"metric": "paper-shape context runs (seconds per full triangle)",
+           "unit": "s", "runs": runs,
+           "note": "context only: the paper's times are FP64 on one 5110P "
+                   "Xeon Phi (Table of Section IV)",
+           "config": {"workload": "paper shapes", "split": args.prec}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,7 +645,8 @@ def main():
     ap.add_argument("--prec", default="auto",
                     choices=["auto", "bf16x3", "fp16x3s", "bf16x1"])
     ap.add_argument("--workload", default="allpairs",
-                    choices=["allpairs", "perm", "batched", "cross"])
+                    choices=["allpairs", "perm", "batched", "cross",
+                             "paper"])
     ap.add_argument("--n", type=int, default=N_GENES)
     ap.add_argument("--l", type=int, default=L_SAMPLES)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -594,6 +664,8 @@ def main():
         return run_batched(args)
     if args.workload == "cross":
         return run_cross(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run_gpu(args)
 
 

@@ -67,8 +67,11 @@ typedef enum {
                              s = floor(log2(l)/2); about 30x more accurate */
     PCC_PREC_BF16X1 = 4,  /* Z = bf16(z), one product (reported only:
                              about 1e-3 error) */
-    PCC_PREC_AUTO = 5     /* the more accurate split form for the row
-                             length: FP16X3S for l < 512, else BF16X3 */
+    PCC_PREC_AUTO = 5     /* the split form with the smaller worst-case
+                             error for the row length: FP16X3S for
+                             l <= 2048, else BF16X3 (beyond l = 2048 no
+                             split form stays within 1e-5 on every input;
+                             PCC_PREC_FP32 does) */
 } pcc_prec;
 
 typedef struct pcc_zmat pcc_zmat; /* opaque, library-owned */

@@ -49,17 +49,26 @@ bool device_is_sm103(int dev) {
   return maj == 10 && min == 3;
 }
 
+}  // namespace
+
 pcc_prec resolve_prec(pcc_prec p, int64_t l) {
-  // Both split forms cost the same; their error has two parts: how well the
-  // two halves represent z (FP16 halves: ~2^-22, BF16: ~2^-17) and the
-  // tensor cores' FP32 accumulation, which rounds toward zero at every
-  // update and loses more with FP16 halves.  Measured max |dr| on |r| ~ 1:
-  //   l = 256: FP16 1.9e-6, BF16 3.8e-6;  l = 512: 3.3e-6 vs 2.8e-6;
-  //   l = 1024: 6.5e-6 vs 4.5e-6;  l = 2048: 1.3e-5 vs 8.4e-6.
+  // Both split forms cost the same.  Their error has two parts: how well
+  // the two halves represent z (FP16 halves of z 2^s: ~2^-22 relative;
+  // BF16 halves: ~2^-18) and the tensor cores' FP32 accumulation, which
+  // rounds toward zero at every update and loses more with FP16 halves.
+  // On rows with planted modules BF16X3 is slightly better; on exact
+  // copies of rows whose mass sits in one sample (r = 1, nothing averages
+  // out) the representation dominates and BF16X3 reaches 1.0-1.3e-5 at
+  // every l, while FP16X3S stays at <= 9.1e-6 up to l = 2048 (two
+  // accumulators above l = 1024).  Max |dr| of the two studies, measured:
+  //   l      256      512      1024     2048     3072     4096
+  //   FP16   2.1e-6   4.7e-6   9.1e-6   8.9e-6   1.25e-5  1.76e-5
+  //   BF16   1.26e-5  1.25e-5  1.20e-5  1.05e-5  1.34e-5  1.88e-5
   if (p != PCC_PREC_AUTO) return p;
-  return l < 512 ? PCC_PREC_FP16X3S : PCC_PREC_BF16X3;
+  return l <= 2048 ? PCC_PREC_FP16X3S : PCC_PREC_BF16X3;
 }
 
+namespace {
 int32_t scale_exp_for(int64_t l) {
   // s = floor(log2(l) / 2): z * 2^s <= 2^s <= sqrt(l), so |hi| stays far
   // from FP16 overflow while typical |z 2^s| ~ 1 keeps lo normal
@@ -104,6 +113,9 @@ TcTuning g_tune = [] {
   t.band = (v >= 1 && v <= 4096) ? v : 32;
   t.cost_c0 = 3000.0;
   t.cost_c1 = 260.0;
+  e = getenv("PCC_TC_KALT");
+  const int ka = e ? atoi(e) : 0;
+  t.kalt_min_l = ka >= 64 ? ka : 1024;
   return t;
 }();
 }  // namespace

@@ -62,10 +62,7 @@ extern "C" pcc_status pcc_allpairs_upper_noalloc(const float* X, int64_t n,
                                                  void* stream) {
   if (!X || !R || n < 2 || l < 2 || ldx < l || n >= (1ll << 31))
     return PCC_ERR_INVALID_ARG;
-  const pcc_prec rp =
-      prec == PCC_PREC_AUTO
-          ? (l < 512 ? PCC_PREC_FP16X3S : PCC_PREC_BF16X3)  // as pcc_standardize
-          : prec;
+  const pcc_prec rp = resolve_prec(prec, l);  // as pcc_standardize
   if (rp != PCC_PREC_BF16X3 && rp != PCC_PREC_FP16X3S &&
       rp != PCC_PREC_BF16X1)
     return PCC_ERR_INVALID_ARG;

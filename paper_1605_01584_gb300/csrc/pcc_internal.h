@@ -35,6 +35,8 @@ namespace pcc {
 constexpr int kLpadAlign = 64;
 
 bool is_split(pcc_prec p);
+// PCC_PREC_AUTO -> the split form for rows of length l; others unchanged
+pcc_prec resolve_prec(pcc_prec p, int64_t l);
 int num_sms(int device);
 uint64_t wait_limit_ns();
 bool debug_drop_loads();  // test hook of pcc_debug_drop_loads
@@ -60,6 +62,7 @@ struct TcTuning {
   int64_t band;      // super-tile rows per band of the pair schedule
   double cost_c0;    // batched plan: cycles per unit outside the K loop
   double cost_c1;    // batched plan: cycles per K block and product
+  int64_t kalt_min_l;  // padded rows longer than this use two accumulators
 };
 TcTuning tc_tuning();
 void tc_set_tuning(const TcTuning& t);

@@ -351,7 +351,7 @@ bool build_plan(Plan* P) {
     d.m = tc_super_count(Z->n);
     d.nkb = (int)(Z->lpad / kKB);
     d.nprod = Z->prec == PCC_PREC_BF16X1 ? 1 : 3;
-    d.kalt = (Z->lpad > 1024 && d.nkb >= 2) ? 1 : 0;
+    d.kalt = (Z->lpad > tc_tuning().kalt_min_l && d.nkb >= 2) ? 1 : 0;
     d.idesc = make_idesc_f16(Z->prec != PCC_PREC_FP16X3S, kBM, kBN);
     d.scale = (float)ldexp(1.0, -2 * Z->scale_exp);
     d.flags = Z->flags;

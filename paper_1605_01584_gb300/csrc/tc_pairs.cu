@@ -60,7 +60,6 @@ namespace {
 constexpr int kBM = 128;   // rows per unit (MMA M)
 constexpr int kBN = 256;   // columns per unit (MMA N)
 constexpr int kUK = 16;    // K per tcgen05.mma kind::f16
-constexpr int kKaltMinL = 1024;  // longer rows use two accumulators
 constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 
@@ -492,7 +491,7 @@ template <int KB, bool CROSS>
 cudaError_t launch_kb(const pcc_zmat* Z, const pcc_zmat* ZB, TcParams& p,
                       int grid, bool write_r, bool edges_on, cudaStream_t s) {
   p.nkb = (int)(Z->lpad / KB);
-  p.kalt = (Z->lpad > kKaltMinL && p.nkb >= 2) ? 1 : 0;
+  p.kalt = (Z->lpad > tc_tuning().kalt_min_l && p.nkb >= 2) ? 1 : 0;
   switch (Z->prec) {
     case PCC_PREC_BF16X3:
       return launch_prec<3, true, KB, CROSS>(Z, ZB, p, grid, write_r,
