@@ -429,7 +429,7 @@ def run_perm(args):
     import paper_1605_01584_gb300 as pcc
     import synth
     pcc.load()
-    n, l, P = 4096, 256, 1000
+    n, l, P = 4096, 256, args.P
     X = synth.counts_log(n, l, 4)
     perms = synth.fisher_yates_perms(P, l, seed=4)
     Xd = torch.from_numpy(X).cuda()
@@ -454,7 +454,7 @@ def run_perm(args):
            "unit": "Gpair*samples*perms/s", "ms_per_step": ms,
            "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
            "status": st, "dtype": {2: "bf16", 3: "f16"}.get(info["prec"]),
-           "config": {"workload": "permutation test n=4096 x l=256, P=1000",
+           "config": {"workload": f"permutation test n=4096 x l=256, P={P}",
                       "split": args.prec},
            "roofline_split_executed": {
                "bound": "tensor", "achieved": exec_flops / (ms / 1e3) / 1e12,
@@ -648,6 +648,8 @@ def main():
                     choices=["allpairs", "perm", "batched", "cross",
                              "paper"])
     ap.add_argument("--n", type=int, default=N_GENES)
+    ap.add_argument("--P", type=int, default=1000,
+                    help="permutations of the perm workload")
     ap.add_argument("--l", type=int, default=L_SAMPLES)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-fp32", action="store_true")
