@@ -374,8 +374,14 @@ def run_gpu(args):
             Xd.copy_(Xh, non_blocking=True)
             pcc.pcc_standardize(Xd, args.prec, Z=Z)
             cnt.zero_()
-            pcc.pcc_threshold_edges(Z, TAU, E, EDGE_CAP, cnt, R)
-            Rh.copy_(R, non_blocking=True)
+            if args.e2e_mode == "passes":
+                # row-block passes: each pass's slice of R is copied to Rh
+                # while the next pass computes (Algorithm 2)
+                pcc.pcc_threshold_edges_host(Z, TAU, E, EDGE_CAP, cnt, Rh,
+                                             device_bytes=args.e2e_window)
+            else:
+                pcc.pcc_threshold_edges(Z, TAU, E, EDGE_CAP, cnt, R)
+                Rh.copy_(R, non_blocking=True)
             ch.copy_(cnt, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             ne = min(int(ch.item()), EDGE_CAP)
@@ -393,6 +399,7 @@ def run_gpu(args):
         out["e2e"] = {"value": gpair_samples(n, l) * world / (e2e_ms / 1e3),
                       "unit": UNIT, "ms_per_step": e2e_ms,
                       "h2d_bytes_per_step": X.nbytes,
+                      "mode": args.e2e_mode,
                       "d2h_bytes_per_step": npairs * 4 + 8 + ne * 12}
 
     if rank == 0 and not args.skip_cpu:
@@ -654,6 +661,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--e2e-mode", default="passes",
+                    choices=["passes", "oneshot"],
+                    help="host delivery of R: overlapped row-block passes "
+                         "or one kernel then one copy")
+    ap.add_argument("--e2e-window", type=int, default=0,
+                    help="device bytes for the two pass windows (0: auto)")
     ap.add_argument("--skip-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":

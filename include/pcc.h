@@ -221,6 +221,16 @@ pcc_status pcc_allpairs_upper_host(const pcc_zmat *Z, void *R_host,
                                    pcc_rows_sink sink, void *user,
                                    void *stream);
 
+/* pcc_threshold_edges with R delivered to host memory the same way: the
+ * edge list (device, as pcc_threshold_edges) and the FP32 packed triangle
+ * (R_host or the sink's staged slices) come from the same passes.  Not for
+ * PCC_PREC_FP64. */
+pcc_status pcc_threshold_edges_host(const pcc_zmat *Z, float tau,
+                                    pcc_edge *edges, uint64_t capacity,
+                                    uint64_t *d_count, float *R_host,
+                                    int64_t device_bytes, pcc_rows_sink sink,
+                                    void *user, void *stream);
+
 /* The same for the dense cross matrix: R_host rows of pitch ldr >= ny (a
  * staged slice has pitch ny). */
 pcc_status pcc_cross_allpairs_host(const pcc_zmat *ZX, const pcc_zmat *ZY,

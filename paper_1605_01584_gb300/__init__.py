@@ -98,6 +98,8 @@ def load(path: str | None = None):
                                           _P]),
         "pcc_cross_allpairs_host": (_ST, [_P, _P, _P, _I32, _I64, _I64,
                                           _SINK, _P, _P]),
+        "pcc_threshold_edges_host": (_ST, [_P, ctypes.c_float, _P, _U64, _P,
+                                           _P, _I64, _SINK, _P, _P]),
         "pcc_perm_test": (_ST, [_P, _P, _I32, _I32, _I32, _P, _P]),
         "pcc_allpairs_upper_batched": (_ST, [_P, _I32, _P, _P]),
         "pcc_sync_status": (_ST, [_P, _P]),
@@ -299,6 +301,30 @@ def pcc_allpairs_upper_host(Z: Zmat, R_host=None, device_bytes: int = 0,
             Z.handle, hp, rt, int(device_bytes), cb, None, _stream(stream)),
         elems, 8 if f64 else 4, sink)
     _check(st, "pcc_allpairs_upper_host")
+    return R_host
+
+
+def pcc_threshold_edges_host(Z: Zmat, tau: float, edges, capacity: int,
+                             d_count, R_host=None, device_bytes: int = 0,
+                             sink=None, stream=None):
+    """pcc_threshold_edges with the packed FP32 triangle delivered to host
+    memory in overlapped passes (R_host: numpy/pinned float32 of n(n-1)/2,
+    or a tensor on the host; None with a sink)."""
+    n = Z.info()["n"]
+
+    def elems(r0, r1):
+        return r1 * (2 * n - r1 - 1) // 2 - r0 * (2 * n - r0 - 1) // 2
+
+    hp = None
+    if R_host is not None:
+        hp = ctypes.c_void_p(R_host.data_ptr() if hasattr(R_host, "data_ptr")
+                             else R_host.ctypes.data)
+    st = _host_stream(
+        lambda cb: load().pcc_threshold_edges_host(
+            Z.handle, float(tau), _ptr(edges), int(capacity), _ptr(d_count),
+            hp, int(device_bytes), cb, None, _stream(stream)),
+        elems, 4, sink)
+    _check(st, "pcc_threshold_edges_host")
     return R_host
 
 

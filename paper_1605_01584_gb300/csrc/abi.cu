@@ -295,6 +295,8 @@ pcc_status pcc_zmat_destroy(pcc_zmat* Z) {
   cudaGetDevice(&cur);
   if (cur != Z->device) cudaSetDevice(Z->device);
   if (Z->perm_ws) cudaFree(Z->perm_ws);
+  if (Z->win_ws) cudaFree(Z->win_ws);
+  if (Z->stage_ws) cudaFreeHost(Z->stage_ws);
   cudaError_t e = cudaFree(Z->base);
   if (cur != Z->device) cudaSetDevice(cur);
   free(Z);
@@ -428,6 +430,20 @@ pcc_status pcc_allpairs_upper_host(const pcc_zmat* Z, void* R_host,
   if (rt == PCC_F64 && Z->prec != PCC_PREC_FP64) return PCC_ERR_INVALID_ARG;
   return allpairs_host(Z, nullptr, R_host, rt, 0, device_bytes, sink, user,
                        static_cast<cudaStream_t>(stream));
+}
+
+pcc_status pcc_threshold_edges_host(const pcc_zmat* Z, float tau,
+                                    pcc_edge* edges, uint64_t capacity,
+                                    uint64_t* d_count, float* R_host,
+                                    int64_t device_bytes, pcc_rows_sink sink,
+                                    void* user, void* stream) {
+  if (!Z || !d_count || (capacity > 0 && !edges) || !(tau >= 0.f) ||
+      !isfinite(tau) || (!R_host && !sink) || Z->prec == PCC_PREC_FP64)
+    return PCC_ERR_INVALID_ARG;
+  const HostEdges he{tau, edges, capacity,
+                     reinterpret_cast<unsigned long long*>(d_count)};
+  return allpairs_host(Z, nullptr, R_host, PCC_F32, 0, device_bytes, sink,
+                       user, static_cast<cudaStream_t>(stream), &he);
 }
 
 pcc_status pcc_cross_allpairs_host(const pcc_zmat* ZX, const pcc_zmat* ZY,

@@ -28,6 +28,12 @@ struct pcc_zmat {
   // permutation-test work buffer (allocated by the first pcc_perm_test)
   void* perm_ws;
   size_t perm_ws_bytes;
+  // windows and pinned staging of the host-delivery passes (kept between
+  // calls, grown when a call needs more)
+  void* win_ws;
+  size_t win_ws_bytes;
+  void* stage_ws;
+  size_t stage_ws_bytes;
 };
 
 namespace pcc {
@@ -109,9 +115,16 @@ cudaError_t launch_simt_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, void* R,
 
 // Passes of whole row blocks into two device windows, copied to host memory
 // while the next pass computes (ZB = NULL: the packed triangle of ZA).
+struct HostEdges {   // the edge list written by the same passes
+  float tau;
+  pcc_edge* edges;
+  uint64_t cap;
+  unsigned long long* count;
+};
 pcc_status allpairs_host(const pcc_zmat* ZA, const pcc_zmat* ZB, void* host,
                          pcc_dtype rt, int64_t ldh, int64_t device_bytes,
-                         pcc_rows_sink sink, void* user, cudaStream_t s);
+                         pcc_rows_sink sink, void* user, cudaStream_t s,
+                         const HostEdges* he = nullptr);
 
 // K7: all pairs of B matrices in one persistent launch.
 pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,

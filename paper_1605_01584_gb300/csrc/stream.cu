@@ -103,6 +103,8 @@ bool group(const std::vector<Block>& bl, int64_t n, int64_t cross_cols,
   return true;
 }
 
+// The per-call objects; the windows and staging buffers themselves are
+// cached in the pcc_zmat (grown when a call needs more).
 struct Resources {
   void* win[2] = {nullptr, nullptr};
   void* stage[2] = {nullptr, nullptr};
@@ -112,8 +114,6 @@ struct Resources {
   ~Resources() {
     if (cs) cudaStreamSynchronize(cs);
     for (int k = 0; k < 2; ++k) {
-      if (win[k]) cudaFree(win[k]);
-      if (stage[k]) cudaFreeHost(stage[k]);
       if (k_done[k]) cudaEventDestroy(k_done[k]);
       if (c_done[k]) cudaEventDestroy(c_done[k]);
     }
@@ -121,14 +121,50 @@ struct Resources {
   }
 };
 
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// two windows of `each` bytes in Z's device cache (and two pinned staging
+// buffers when `staging`)
+pcc_status take_workspace(pcc_zmat* Z, size_t each, bool staging,
+                          Resources* r) {
+  const size_t need = 2 * round256(each);
+  if (Z->win_ws_bytes < need) {
+    if (Z->win_ws) cudaFree(Z->win_ws);
+    Z->win_ws = nullptr;
+    Z->win_ws_bytes = 0;
+    if (cudaMalloc(&Z->win_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return PCC_ERR_OOM;
+    }
+    Z->win_ws_bytes = need;
+  }
+  r->win[0] = Z->win_ws;
+  r->win[1] = static_cast<char*>(Z->win_ws) + round256(each);
+  if (staging) {
+    if (Z->stage_ws_bytes < need) {
+      if (Z->stage_ws) cudaFreeHost(Z->stage_ws);
+      Z->stage_ws = nullptr;
+      Z->stage_ws_bytes = 0;
+      if (cudaMallocHost(&Z->stage_ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        return PCC_ERR_OOM;
+      }
+      Z->stage_ws_bytes = need;
+    }
+    r->stage[0] = Z->stage_ws;
+    r->stage[1] = static_cast<char*>(Z->stage_ws) + round256(each);
+  }
+  return PCC_OK;
+}
+
 using LaunchFn =
     std::function<cudaError_t(void* win, const Pass& p, cudaStream_t s)>;
 
 // The pass pipeline.  host: caller's buffer (NULL = staging); ldh: its row
 // pitch for dense output (0 = packed, one contiguous slice per pass);
 // ncols: dense row length on the device.
-pcc_status run_passes(const std::vector<Pass>& passes, size_t esize,
-                      int64_t ncols, void* host, int64_t ldh,
+pcc_status run_passes(pcc_zmat* Zc, const std::vector<Pass>& passes,
+                      size_t esize, int64_t ncols, void* host, int64_t ldh,
                       pcc_rows_sink sink, void* user, cudaStream_t s,
                       const LaunchFn& launch) {
   int64_t wmax = 0;
@@ -137,17 +173,11 @@ pcc_status run_passes(const std::vector<Pass>& passes, size_t esize,
   if (passes.empty() || wmax == 0) return PCC_OK;
   Resources r;
   const int nwin = passes.size() > 1 ? 2 : 1;
-  for (int k = 0; k < nwin; ++k) {
-    if (cudaMalloc(&r.win[k], (size_t)wmax * esize) != cudaSuccess) {
-      cudaGetLastError();
-      return PCC_ERR_OOM;
-    }
-    if (!host && cudaMallocHost(&r.stage[k], (size_t)wmax * esize) !=
-                     cudaSuccess) {
-      cudaGetLastError();
-      return PCC_ERR_OOM;
-    }
-  }
+  // calls return only after their last copy, so Z's cached buffers are
+  // free when the next call starts
+  pcc_status ws = take_workspace(Zc, (size_t)wmax * esize, host == nullptr,
+                                 &r);
+  if (ws != PCC_OK) return ws;
   if (cudaStreamCreateWithFlags(&r.cs, cudaStreamNonBlocking) != cudaSuccess)
     return PCC_ERR_CUDA;
   for (int k = 0; k < 2; ++k)
@@ -226,7 +256,13 @@ int64_t window_cap(int64_t device_bytes, size_t esize) {
 
 pcc_status allpairs_host(const pcc_zmat* ZA, const pcc_zmat* ZB, void* host,
                          pcc_dtype rt, int64_t ldh, int64_t device_bytes,
-                         pcc_rows_sink sink, void* user, cudaStream_t s) {
+                         pcc_rows_sink sink, void* user, cudaStream_t s,
+                         const HostEdges* he) {
+  const bool eo = he != nullptr;
+  const float tau = eo ? he->tau : 0.f;
+  pcc_edge* ed = eo ? he->edges : nullptr;
+  const uint64_t ecap = eo ? he->cap : 0;
+  unsigned long long* cnt = eo ? he->count : nullptr;
   const size_t esize = rt == PCC_F64 ? 8 : 4;
   const int64_t cap = window_cap(device_bytes, esize);
   const int64_t cross = ZB ? ZB->n : 0;
@@ -241,27 +277,29 @@ pcc_status allpairs_host(const pcc_zmat* ZA, const pcc_zmat* ZB, void* host,
       G = (G + 1) / 2;
     }
     return run_passes(
-        passes, esize, cross, host, ZB ? ldh : 0, sink, user, s,
+        const_cast<pcc_zmat*>(ZA), passes, esize, cross, host, ZB ? ldh : 0,
+        sink, user, s,
         [&](void* win, const Pass& q, cudaStream_t st) {
           float* w = static_cast<float*>(win);
           if (ZB)
-            return launch_tc_cross(ZA, ZB, w, cross, q.t0, q.t1, false, 0.f,
-                                   nullptr, 0, nullptr, st, q.e0, G);
-          return launch_tc_pairs(ZA, w, q.t0, q.t1, false, 0.f, nullptr, 0,
-                                 nullptr, st, q.e0, G);
+            return launch_tc_cross(ZA, ZB, w, cross, q.t0, q.t1, eo, tau, ed,
+                                   ecap, cnt, st, q.e0, G);
+          return launch_tc_pairs(ZA, w, q.t0, q.t1, eo, tau, ed, ecap, cnt,
+                                 st, q.e0, G);
         });
   }
   const int64_t BT = simt_tile_size(ZA->prec);
   if (!group(simt_blocks(n, BT, cross), n, cross, cap, &passes))
     return PCC_ERR_OOM;
-  return run_passes(passes, esize, cross, host, ZB ? ldh : 0, sink, user, s,
+  return run_passes(const_cast<pcc_zmat*>(ZA), passes, esize, cross, host,
+                    ZB ? ldh : 0, sink, user, s,
                     [&](void* win, const Pass& q, cudaStream_t st) {
                       if (ZB)
                         return launch_simt_cross(ZA, ZB, win, rt, cross, q.t0,
-                                                 q.t1, 0.f, nullptr, 0,
-                                                 nullptr, st, q.e0);
-                      return launch_simt_pairs(ZA, win, rt, q.t0, q.t1, 0.f,
-                                               nullptr, 0, nullptr, st, q.e0);
+                                                 q.t1, tau, ed, ecap, cnt, st,
+                                                 q.e0);
+                      return launch_simt_pairs(ZA, win, rt, q.t0, q.t1, tau,
+                                               ed, ecap, cnt, st, q.e0);
                     });
 }
 

@@ -135,3 +135,35 @@ def test_cross_host_pitch(pcc_gpu, prec):
     assert np.array_equal(H[:, :ny], want, equal_nan=True)
     ref = oracle.cross_rows(X, Y)
     assert np.nanmax(np.abs(H[:, :ny] - ref)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3s"])
+def test_threshold_edges_host_matches_device_call(pcc_gpu, prec):
+    """Edges and the host triangle from the passes equal one device call:
+    the same edge set (order aside) and the same R bits."""
+    import torch
+    pcc = pcc_gpu
+    n, l, tau = 1400, 64, 0.6
+    X = synth.counts_log(n, l, 27, dtype=np.float32)
+    Z = _z(pcc, X, prec)
+    cap = 1 << 18
+    E1 = torch.zeros(cap * 12, dtype=torch.uint8, device="cuda")
+    E2 = torch.zeros_like(E1)
+    c1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    c2 = torch.zeros_like(c1)
+    R1 = torch.full((n * (n - 1) // 2,), 7.0, device="cuda")
+    pcc.pcc_threshold_edges(Z, tau, E1, cap, c1, R1)
+    H = np.full(n * (n - 1) // 2, 7.0, dtype=np.float32)
+    passes = []
+    pcc.pcc_threshold_edges_host(Z, tau, E2, cap, c2, H,
+                                 device_bytes=3 << 20,
+                                 sink=lambda a, b, v: passes.append(a))
+    assert pcc.pcc_sync_status(Z) == 0
+    assert len(passes) >= 3
+    k1, k2 = int(c1.item()), int(c2.item())
+    assert k1 == k2 and k1 > 100
+    def edge_set(E, k):
+        rec = E[:k * 12].cpu().numpy().view(np.uint32).reshape(-1, 3)
+        return set(map(tuple, rec.tolist()))
+    assert edge_set(E1, k1) == edge_set(E2, k2)
+    assert np.array_equal(H, R1.cpu().numpy(), equal_nan=True)
