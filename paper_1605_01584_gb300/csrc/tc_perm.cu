@@ -16,13 +16,19 @@
 //                  and column by column so that concurrent CTAs reuse the
 //                  same permuted column panels from L2.  Per item: the A
 //                  rows (z_i, hi and lo) are loaded once into shared memory
-//                  and stay resident; the unpermuted B rows give r_obs and
-//                  then each permutation's B rows (from the workspace, a 3-D
-//                  TMA map) give r_k, all as the 3-product split contraction
-//                  into a double-buffered TMEM accumulator.  The epilogue
-//                  keeps |r_obs| and 16-bit counts in registers (thread = row
-//                  i, 64 columns j) and adds the counts to the packed output
-//                  with one atomic per pair and item.
+//                  and stay resident; the unpermuted B rows give r_obs, and
+//                  then the B rows of two permutations at a time (from the
+//                  workspace, a 3-D TMA map), stacked into one 256-row
+//                  operand, give r_k and r_k+1 with one N = 256 MMA per
+//                  K step and product (the 3-product split contraction,
+//                  into a double-buffered 128 x 256 TMEM accumulator).  At
+//                  N = 128 the same work took twice the instructions and
+//                  was bound by the MMA issue, not by the operand stream.
+//                  The epilogue keeps |r_obs| and 16-bit counts in
+//                  registers (thread = row i, 64 columns j, both
+//                  permutations of a pass against the same |r_obs|) and
+//                  adds the counts to the packed output with one atomic per
+//                  pair and item.
 // Same roles and bounded waits as the pair kernel (tc_pairs.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -36,13 +42,15 @@
 namespace pcc {
 namespace {
 
-constexpr int kPT = 128;      // tile side (MMA M = N = 128)
+constexpr int kPT = 128;      // tile side (MMA M; N = 128 per permutation)
 constexpr int kPK = 32;       // K per stage (64-B swizzle rows)
 constexpr int kPUK = 16;
 constexpr int kPThreads = 320;
 constexpr int kPEpiWarps = 8;
 constexpr int kPTile = kPT * kPK * 2;        // 8 KB: 128 rows x 32 (16-bit)
-constexpr int kPStageB = 2 * kPTile;         // B hi + lo
+constexpr int kPBHalf = 2 * kPTile;          // B hi (or lo): 256 rows, 16 KB
+constexpr int kPStageB = 2 * kPBHalf;        // B hi + lo of two permutations
+constexpr int kPAcc = 2 * kPT;               // TMEM columns per accumulator
 constexpr int kPMaxResidentK = 256;          // resident A up to lpad 256
 constexpr int kPSmemBudget = 232448;
 constexpr int64_t kPermChunk = 48;           // permutations per work item
@@ -78,7 +86,9 @@ template <bool RESA>
 struct PCfg {
   // resident A: nkb blocks x (hi + lo) tiles, at most kPMaxResidentK / kPK
   static constexpr int kABytes = RESA ? (kPMaxResidentK / kPK) * 2 * kPTile : 0;
-  static constexpr int kStageBytes = RESA ? kPStageB : 2 * kPStageB;
+  // stage: [B hi | B lo], 256 rows each (two permutations), streamed A in
+  // front of them
+  static constexpr int kStageBytes = RESA ? kPStageB : 2 * kPTile + kPStageB;
   static constexpr int kBarBytes = 256;
   static constexpr int kStages =
       (kPSmemBudget - 1024 - kABytes - kBarBytes) / kStageBytes > 8
@@ -168,7 +178,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
               const __grid_constant__ CUtensorMap tp_lo, const PermParams p) {
   using C = PCfg<RESA>;
   constexpr int S = C::kStages;
-  constexpr uint32_t kIdesc = make_idesc_f16(BF16, kPT, kPT);
+  // N = 128: r_obs and a lone last permutation; N = 256: two permutations
+  constexpr uint32_t kIdesc1 = make_idesc_f16(BF16, kPT, kPT);
+  constexpr uint32_t kIdesc2 = make_idesc_f16(BF16, kPT, 2 * kPT);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -187,11 +199,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
-  // stage layout: RESA: [B hi | B lo]; else [A hi | A lo | B hi | B lo]
+  // stage layout: RESA: [B hi | B lo]; else [A hi | A lo | B hi | B lo];
+  // B hi and lo hold 256 rows each: the first permutation's 128 rows, then
+  // the second's (or the unpermuted rows alone in the first 128)
   auto sB_hi = [&](int s) {
     return ring + s * C::kStageBytes + (RESA ? 0 : 2 * kPTile);
   };
-  auto sB_lo = [&](int s) { return sB_hi(s) + kPTile; };
+  auto sB_lo = [&](int s) { return sB_hi(s) + kPBHalf; };
   auto sA_hi = [&](int s, int kb) {
     return RESA ? aregion + kb * 2 * kPTile : ring + s * C::kStageBytes;
   };
@@ -272,13 +286,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
           aph ^= 1u;
         }
-        for (int pass = -1; pass < klen && ok; ++pass) {
+        // pass -1: r_obs; pass q: permutations k0 + 2q and (if any) + 1
+        const int npass = (klen + 1) / 2;
+        for (int pass = -1; pass < npass && ok; ++pass) {
+          const bool two = pass >= 0 && 2 * pass + 1 < klen;
+          const uint32_t bytes = (RESA ? 0u : 2u * kPTile) +
+                                 (two ? 4u : 2u) * (uint32_t)kPTile;
           for (int kb = 0; kb < p.nkb; ++kb) {
             if (!mbar_wait(&empty[stage], phase ^ 1u, w)) {
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
+            mbar_arrive_expect_tx(&full[stage], bytes);
             const int kc = kb * kPK;
             if (!RESA) {
               tma_load_2d_hint(sA_hi(stage, kb), &tz_hi, &full[stage], kc,
@@ -292,10 +311,17 @@ __global__ void __launch_bounds__(kPThreads, 1)
               tma_load_2d_hint(sB_lo(stage), &tz_lo, &full[stage], kc,
                                (int)col0, pol);
             } else {
+              const int ka = k0 + 2 * pass;
               tma_load_3d(sB_hi(stage), &tp_hi, &full[stage], kc, (int)col0,
-                          k0 + pass);
+                          ka);
               tma_load_3d(sB_lo(stage), &tp_lo, &full[stage], kc, (int)col0,
-                          k0 + pass);
+                          ka);
+              if (two) {
+                tma_load_3d(sB_hi(stage) + kPTile, &tp_hi, &full[stage], kc,
+                            (int)col0, ka + 1);
+                tma_load_3d(sB_lo(stage) + kPTile, &tp_lo, &full[stage], kc,
+                            (int)col0, ka + 1);
+              }
             }
             issued_mask |= 1u << stage;
             last_phase[stage] = phase;
@@ -331,13 +357,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
           if (!mbar_wait(afull, aph, w)) break;
           aph ^= 1u;
         }
-        for (int pass = -1; pass < klen && ok; ++pass) {
+        const int npass = (klen + 1) / 2;
+        for (int pass = -1; pass < npass && ok; ++pass) {
+          const bool two = pass >= 0 && 2 * pass + 1 < klen;
+          const uint32_t idesc = two ? kIdesc2 : kIdesc1;
           if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kPT);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kPAcc);
           for (int kb = 0; kb < p.nkb; ++kb) {
             if (!mbar_wait(&full[stage], phase, w)) {
               ok = false;
@@ -355,9 +384,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
               const uint64_t dBH = kmajor_desc<64>(bH + off);
               const uint64_t dAL = kmajor_desc<64>(aL + off);
               const uint64_t dBL = kmajor_desc<64>(bL + off);
-              umma_f16(d_tmem, dAH, dBH, kIdesc, (kb | ks) != 0);
-              umma_f16(d_tmem, dAH, dBL, kIdesc, 1u);
-              umma_f16(d_tmem, dAL, dBH, kIdesc, 1u);
+              umma_f16(d_tmem, dAH, dBH, idesc, (kb | ks) != 0);
+              umma_f16(d_tmem, dAH, dBL, idesc, 1u);
+              umma_f16(d_tmem, dAL, dBH, idesc, 1u);
             }
             umma_commit(&empty[stage]);
             if (++stage == S) {
@@ -395,7 +424,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
       uint32_t cnt[32];  // two 16-bit counts per word
 #pragma unroll
       for (int t = 0; t < 32; ++t) cnt[t] = 0u;
-      for (int pass = -1; pass < klen; ++pass) {
+      const int npass = (klen + 1) / 2;
+      for (int pass = -1; pass < npass; ++pass) {
+        // permutations in this accumulator: columns [0, 128) and, for a
+        // pair, [128, 256); this warp reads columns 64h.. of each
+        const int nperm = pass < 0 ? 1 : (2 * pass + 1 < klen ? 2 : 1);
         bool got = true;
         if (lane == 0) got = mbar_wait(&tfull[acc], aphase, w);
         if (!__shfl_sync(0xffffffffu, got ? 1 : 0, 0)) {
@@ -404,22 +437,25 @@ __global__ void __launch_bounds__(kPThreads, 1)
         }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) +
-                               (uint32_t)(acc * kPT + h * 64);
+                               (uint32_t)(acc * kPAcc + h * 64);
+        for (int e = 0; e < nperm; ++e) {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          uint32_t v[32];
-          tmem_ld_32x32b_x32(taddr + (uint32_t)(c * 32), v);
-          tmem_ld_wait();
-          if (pass < 0) {
+          for (int c = 0; c < 2; ++c) {
+            uint32_t v[32];
+            tmem_ld_32x32b_x32(taddr + (uint32_t)(e * kPT + c * 32), v);
+            tmem_ld_wait();
+            if (pass < 0) {
 #pragma unroll
-            for (int t = 0; t < 32; ++t)
-              robs[c * 32 + t] = fabsf(__uint_as_float(v[t]));
-          } else {
+              for (int t = 0; t < 32; ++t)
+                robs[c * 32 + t] = fabsf(__uint_as_float(v[t]));
+            } else {
 #pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              const uint32_t hit =
-                  fabsf(__uint_as_float(v[t])) >= robs[c * 32 + t] ? 1u : 0u;
-              cnt[c * 16 + (t >> 1)] += hit << ((t & 1) * 16);
+              for (int t = 0; t < 32; ++t) {
+                const uint32_t hit =
+                    fabsf(__uint_as_float(v[t])) >= robs[c * 32 + t] ? 1u
+                                                                     : 0u;
+                cnt[c * 16 + (t >> 1)] += hit << ((t & 1) * 16);
+              }
             }
           }
         }
