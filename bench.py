@@ -661,7 +661,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--e2e-mode", default="oneshot",
+    ap.add_argument("--e2e-mode", default="passes",
                     choices=["passes", "oneshot"],
                     help="host delivery of R: overlapped row-block passes "
                          "or one kernel then one copy")

@@ -255,6 +255,22 @@ def pcc_cross_edges(ZX: Zmat, ZY: Zmat, tau: float, edges, capacity: int,
            "pcc_cross_edges")
 
 
+def _host_buffer(R_host):
+    """(pointer, is_float64, elements) of a contiguous host buffer given as
+    a numpy array or a CPU torch tensor (pinned for overlapped copies)."""
+    import numpy as np
+    if R_host is None:
+        return None, False, 0
+    if hasattr(R_host, "data_ptr"):
+        import torch
+        assert not R_host.is_cuda and R_host.is_contiguous()
+        return (ctypes.c_void_p(R_host.data_ptr()),
+                R_host.dtype == torch.float64, R_host.numel())
+    assert R_host.flags.c_contiguous
+    return (ctypes.c_void_p(R_host.ctypes.data), R_host.dtype == np.float64,
+            R_host.size)
+
+
 def _host_stream(call, n_rows_elems, esize, sink):
     """Run a host-streaming entry point with a Python sink(r0, r1, view)."""
     import numpy as np
@@ -284,18 +300,16 @@ def pcc_allpairs_upper_host(Z: Zmat, R_host=None, device_bytes: int = 0,
     """The packed triangle into host memory in overlapped passes; R_host a
     numpy float32 array of n(n-1)/2 (float64 for the FP64 form) or None
     with a sink(row_begin, row_end, slice) taking each packed slice."""
-    import numpy as np
     info = Z.info()
     n = info["n"]
-    f64 = R_host is not None and R_host.dtype == np.float64
+    hp, f64, size = _host_buffer(R_host)
     rt = PCC_F64 if f64 else PCC_F32
     if R_host is not None:
-        assert R_host.flags.c_contiguous and R_host.size == n * (n - 1) // 2
+        assert size == n * (n - 1) // 2
 
     def elems(r0, r1):
         return r1 * (2 * n - r1 - 1) // 2 - r0 * (2 * n - r0 - 1) // 2
 
-    hp = None if R_host is None else ctypes.c_void_p(R_host.ctypes.data)
     st = _host_stream(
         lambda cb: load().pcc_allpairs_upper_host(
             Z.handle, hp, rt, int(device_bytes), cb, None, _stream(stream)),
@@ -315,10 +329,7 @@ def pcc_threshold_edges_host(Z: Zmat, tau: float, edges, capacity: int,
     def elems(r0, r1):
         return r1 * (2 * n - r1 - 1) // 2 - r0 * (2 * n - r0 - 1) // 2
 
-    hp = None
-    if R_host is not None:
-        hp = ctypes.c_void_p(R_host.data_ptr() if hasattr(R_host, "data_ptr")
-                             else R_host.ctypes.data)
+    hp, _, _ = _host_buffer(R_host)
     st = _host_stream(
         lambda cb: load().pcc_threshold_edges_host(
             Z.handle, float(tau), _ptr(edges), int(capacity), _ptr(d_count),
@@ -332,13 +343,19 @@ def pcc_cross_allpairs_host(ZX: Zmat, ZY: Zmat, R_host=None,
                             device_bytes: int = 0, sink=None, stream=None):
     """Dense cross matrix into host memory in overlapped passes; R_host a
     2-D numpy array (nx x >= ny, unit inner stride) or None with a sink."""
-    import numpy as np
     ny = ZY.info()["n"]
-    f64 = R_host is not None and R_host.dtype == np.float64
+    hp, f64, _ = (_host_buffer(R_host) if R_host is None
+                  or hasattr(R_host, "data_ptr") else
+                  (ctypes.c_void_p(R_host.ctypes.data),
+                   R_host.dtype.itemsize == 8, R_host.size))
     rt = PCC_F64 if f64 else PCC_F32
     esize = 8 if f64 else 4
-    ldr = ny if R_host is None else R_host.strides[0] // esize
-    hp = None if R_host is None else ctypes.c_void_p(R_host.ctypes.data)
+    if R_host is None:
+        ldr = ny
+    elif hasattr(R_host, "data_ptr"):
+        ldr = R_host.stride(0)
+    else:
+        ldr = R_host.strides[0] // esize
     st = _host_stream(
         lambda cb: load().pcc_cross_allpairs_host(
             ZX.handle, ZY.handle, hp, rt, int(ldr), int(device_bytes), cb,

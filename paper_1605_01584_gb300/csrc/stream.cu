@@ -240,16 +240,20 @@ pcc_status run_passes(pcc_zmat* Zc, const std::vector<Pass>& passes,
   return PCC_OK;
 }
 
+// elements per window: half the budget (both windows share it); default
+// budget a quarter of the free device memory, at most 4 GiB
 int64_t window_cap(int64_t device_bytes, size_t esize) {
-  if (device_bytes > 0) return device_bytes / 2 / (int64_t)esize;
-  size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-    cudaGetLastError();
-    fr = (size_t)1 << 32;
+  int64_t b = device_bytes;
+  if (b <= 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = (size_t)1 << 32;
+    }
+    b = (int64_t)(fr / 4);
+    if (b > ((int64_t)4 << 30)) b = (int64_t)4 << 30;
   }
-  int64_t b = (int64_t)(fr / 4);
-  if (b > ((int64_t)4 << 30)) b = (int64_t)4 << 30;
-  return b / (int64_t)esize;
+  return b / 2 / (int64_t)esize;
 }
 
 }  // namespace
