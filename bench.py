@@ -42,6 +42,10 @@ METRIC = ("all-pairs PCC Gpair·samples/s, split-TC vs plain FP32 GPU at "
           "max|Δr|≤1e-5")
 UNIT = "Gpair*samples/s"
 WORKLOAD = "output-bound all-pairs PCC, n=65536 x l=512 FP32"
+# resolved pcc_prec -> (name, tensor-core products per K step, MMA dtype)
+FORMS = {0: ("fp64", 0, "f64"), 1: ("fp32", 0, "f32"),
+         2: ("bf16x3", 3, "bf16"), 3: ("fp16x3s", 3, "f16"),
+         4: ("bf16x4", 4, "bf16"), 5: ("bf16x1", 1, "bf16")}
 
 
 def gpair_samples(n, l):
@@ -295,12 +299,12 @@ def run_gpu(args):
     # roofline of the dominant kernel (the fused pair kernel)
     hbm, bf16, bf16_sus, peak_kind = peaks()
     info = Z.info()
-    z_bytes = n * info["lpad"] * 2 * (1 if info["prec"] == 4 else 2)
+    z_bytes = n * info["lpad"] * 2 * (1 if FORMS[info["prec"]][1] == 1 else 2)
     alg_bytes = npairs * 4 + z_bytes + n + min(edges_found, EDGE_CAP) * 12
     pair_avg = statistics.mean(pair_ms)
     achieved_gbs = alg_bytes / (pair_avg / 1e3) / 1e9
     alg_flops = 2.0 * npairs * l
-    nprod = 1 if info["prec"] == 4 else 3
+    nprod = FORMS[info["prec"]][1]
     exec_flops = nprod * 2.0 * (info["lpad"]) * 128 * 256 * 2 * (
         (-(-n // 256)) * (-(-n // 256) + 1) // 2)
     exec_tflops = exec_flops / (pair_avg / 1e3) / 1e12
@@ -310,11 +314,10 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {2: "bf16", 3: "f16", 4: "bf16"}.get(info["prec"], "?"),
+        "dtype": FORMS[info["prec"]][2],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "l": l, "tau": TAU,
-                   "split": {2: "bf16x3", 3: "fp16x3s",
-                             4: "bf16x1"}.get(info["prec"], args.prec),
+                   "split": FORMS[info["prec"]][0],
                    "seed": SEED,
                    "per_rank": "independent matrix per GPU (seed + 1000*rank)",
                    "l2": "inputs larger than L2 (134 MB X; 8.6 GB output "
@@ -454,13 +457,13 @@ def run_perm(args):
     st = pcc.pcc_sync_status(Z)
     info = Z.info()
     tiles = (-(-n // 128)) * (-(-n // 128) + 1) // 2
-    exec_flops = 3 * 2 * 128 * 128 * info["lpad"] * tiles * (P + 1)
+    exec_flops = FORMS[info["prec"]][1] * 2 * 128 * 128 * info["lpad"] * tiles * (P + 1)
     _, bf16, bf16_sus, kind = peaks()
     out = {"metric": "permutation-test Gpair*samples*perms/s",
            "value": n * (n - 1) / 2 * l * P / (ms / 1e3) / 1e9,
            "unit": "Gpair*samples*perms/s", "ms_per_step": ms,
            "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
-           "status": st, "dtype": {2: "bf16", 3: "f16"}.get(info["prec"]),
+           "status": st, "dtype": FORMS[info["prec"]][2],
            "config": {"workload": f"permutation test n=4096 x l=256, P={P}",
                       "split": args.prec},
            "roofline_split_executed": {
@@ -551,7 +554,7 @@ def run_cross(args):
     st = pcc.pcc_sync_status(ZX)
     info = ZX.info()
     tiles = pcc.pcc_cross_num_tiles(ZX, ZY)
-    nprod = 1 if info["prec"] == 4 else 3
+    nprod = FORMS[info["prec"]][1]
     exec_flops = nprod * 2 * 256 * 256 * info["lpad"] * tiles
     out_bytes = nx * ny * 4 + 2 * 2 * (nx + ny) * info["lpad"]
     hbm, bf16, bf16_sus, kind = peaks()
@@ -559,8 +562,7 @@ def run_cross(args):
            "value": nx * ny * l / (ms / 1e3) / 1e9,
            "unit": "Gpair*samples/s", "ms_per_step": ms,
            "ms_cross_kernel": ms_k, "steps": steps, "warmup": args.warmup,
-           "status": st, "dtype": {2: "bf16", 3: "f16", 4: "bf16"}.get(
-               info["prec"]),
+           "status": st, "dtype": FORMS[info["prec"]][2],
            "config": {"workload": f"cross X {nx}x{l} vs Y {ny}x{l}, dense "
                       "FP32 R", "split": args.prec,
                       "l2": "inputs and the 8.6 GB output exceed L2"},
@@ -624,8 +626,7 @@ def run_paper(args):
             err = float(np.max(np.abs(got[ok] - want[ok])))
             info = Z.info()
             runs.append({"data": name, "n": n, "l": l,
-                         "form": {0: "fp64", 1: "fp32", 2: "bf16x3",
-                                  3: "fp16x3s", 4: "bf16x1"}[info["prec"]],
+                         "form": FORMS[info["prec"]][0],
                          "seconds": ms / 1e3, "status": st,
                          "max_abs_dr_sampled": err,
                          "Gpair_samples_per_s": n * (n - 1) / 2 * l
@@ -650,7 +651,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--prec", default="auto",
-                    choices=["auto", "bf16x3", "fp16x3s", "bf16x1"])
+                    choices=["auto", "bf16x3", "fp16x3s", "bf16x4",
+                             "bf16x1"])
     ap.add_argument("--workload", default="allpairs",
                     choices=["allpairs", "perm", "batched", "cross",
                              "paper"])

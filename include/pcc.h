@@ -65,9 +65,11 @@ typedef enum {
                              hi.hi + hi.lo + lo.hi, FP32 accumulation */
     PCC_PREC_FP16X3S = 3, /* as BF16X3 with FP16 halves of z * 2^s,
                              s = floor(log2(l)/2); about 30x more accurate */
-    PCC_PREC_BF16X1 = 4,  /* Z = bf16(z), one product (reported only:
+    PCC_PREC_BF16X4 = 4,  /* as BF16X3 plus the lo.lo product (4 MMAs per
+                             K step instead of 3) */
+    PCC_PREC_BF16X1 = 5,  /* Z = bf16(z), one product (reported only:
                              about 1e-3 error) */
-    PCC_PREC_AUTO = 5     /* the split form with the smaller worst-case
+    PCC_PREC_AUTO = 6     /* the split form with the smaller worst-case
                              error for the row length: FP16X3S for
                              l <= 2048, else BF16X3 (beyond l = 2048 no
                              split form stays within 1e-5 on every input;
@@ -277,7 +279,8 @@ pcc_status pcc_allpairs_upper_batched(const pcc_zmat *const *Zs, int32_t B,
  * pcc_allpairs_upper do, but keeps the standardized matrix in one
  * file-scope device array of 32 MiB that every device holds from the time
  * it loads the library until the process exits.
- *   prec      PCC_PREC_BF16X3, PCC_PREC_FP16X3S, PCC_PREC_BF16X1 or
+ *   prec      PCC_PREC_BF16X3, PCC_PREC_FP16X3S, PCC_PREC_BF16X4,
+ *             PCC_PREC_BF16X1 or
  *             PCC_PREC_AUTO (tensor-core forms only).
  *   d_status  optional device int32 (caller-owned, may be NULL) set to 0 by
  *             the call and then to PCC_ERR_TIMEOUT if a device wait ran out.

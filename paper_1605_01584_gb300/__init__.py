@@ -34,12 +34,14 @@ PCC_PREC_FP64 = 0
 PCC_PREC_FP32 = 1
 PCC_PREC_BF16X3 = 2
 PCC_PREC_FP16X3S = 3
-PCC_PREC_BF16X1 = 4
-PCC_PREC_AUTO = 5
+PCC_PREC_BF16X4 = 4
+PCC_PREC_BF16X1 = 5
+PCC_PREC_AUTO = 6
 
 PREC_NAMES = {"fp64": PCC_PREC_FP64, "fp32": PCC_PREC_FP32,
               "bf16x3": PCC_PREC_BF16X3, "fp16x3s": PCC_PREC_FP16X3S,
-              "bf16x1": PCC_PREC_BF16X1, "auto": PCC_PREC_AUTO}
+              "bf16x4": PCC_PREC_BF16X4, "bf16x1": PCC_PREC_BF16X1,
+              "auto": PCC_PREC_AUTO}
 
 EDGE_BYTES = 12  # pcc_edge {u32 i, u32 j, f32 r}
 

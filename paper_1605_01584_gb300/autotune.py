@@ -125,7 +125,7 @@ def tune_pairs(n: int, l: int, prec: str = "auto", candidates=None,
     g = torch.Generator(device="cuda").manual_seed(seed)
     X = torch.rand((n, l), device="cuda", generator=g)
     Z = pcc_standardize(X, prec)
-    resolved = {2: "bf16x3", 3: "fp16x3s", 4: "bf16x1"}.get(
+    resolved = {2: "bf16x3", 3: "fp16x3s", 4: "bf16x4", 5: "bf16x1"}.get(
         Z.info()["prec"], str(prec))
     R = torch.empty(n * (n - 1) // 2, device="cuda")
     before = pcc_get_tuning()

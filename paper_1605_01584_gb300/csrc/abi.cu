@@ -80,7 +80,7 @@ int32_t scale_exp_for(int64_t l) {
 
 bool is_split(pcc_prec p) {
   return p == PCC_PREC_BF16X3 || p == PCC_PREC_FP16X3S ||
-         p == PCC_PREC_BF16X1;
+         p == PCC_PREC_BF16X4 || p == PCC_PREC_BF16X1;
 }
 
 int num_sms(int device) {

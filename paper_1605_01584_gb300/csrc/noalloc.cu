@@ -64,7 +64,7 @@ extern "C" pcc_status pcc_allpairs_upper_noalloc(const float* X, int64_t n,
     return PCC_ERR_INVALID_ARG;
   const pcc_prec rp = resolve_prec(prec, l);  // as pcc_standardize
   if (rp != PCC_PREC_BF16X3 && rp != PCC_PREC_FP16X3S &&
-      rp != PCC_PREC_BF16X1)
+      rp != PCC_PREC_BF16X4 && rp != PCC_PREC_BF16X1)
     return PCC_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)

@@ -312,6 +312,7 @@ cudaError_t launch_mode(const TX* X, int64_t ldx, pcc_zmat* Z,
       const float* Xf = reinterpret_cast<const float*>(X);
       switch (Z->prec) {
         case PCC_PREC_BF16X3:
+        case PCC_PREC_BF16X4:  // the same halves; the pair kernel differs
           launch_f32v<M_BF16X3>(Xf, ldx, Z, (int)blocks, 1.f, Z->hi, Z->lo, s);
           break;
         case PCC_PREC_FP16X3S:
@@ -331,6 +332,7 @@ cudaError_t launch_mode(const TX* X, int64_t ldx, pcc_zmat* Z,
   }
   switch (Z->prec) {
     case PCC_PREC_BF16X3:
+    case PCC_PREC_BF16X4:
       k_standardize<TX, M_BF16X3><<<(int)blocks, threads, 0, s>>>(
           X, Z->n, Z->l, ldx, Z->lpad, 1.f, Z->hi, Z->lo, Z->flags);
       break;

@@ -46,7 +46,7 @@ struct alignas(64) MatDesc {
   int64_t n;
   int64_t m;          // super-tiles per side
   int nkb;            // K blocks of 32
-  int nprod;          // 3 or 1
+  int nprod;          // 4, 3 or 1 products per K step
   int kalt;           // even/odd K blocks in two accumulators (long rows)
   uint32_t idesc;     // MMA instruction descriptor (BF16 or FP16 halves)
   float scale;        // accumulator -> r
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         coords(wk, p.items[it], d, &row0, &col0);
         const int nkb = d->nkb, nprod = d->nprod;
         const uint32_t bytes =
-            nprod == 3 ? (uint32_t)kStageBytes : (uint32_t)(kTileA + kTileB);
+            nprod >= 3 ? (uint32_t)kStageBytes : (uint32_t)(kTileA + kTileB);
         for (int kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, w)) {
             ok = false;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                            (int)col0, pol);
           tma_load_2d_hint(sB_hi(stage) + kTileA, &d->tm_hi, &full[stage], kc,
                            (int)col0 + kBM, pol);
-          if (nprod == 3) {
+          if (nprod >= 3) {
             tma_load_2d_hint(sA_lo(stage), &d->tm_lo, &full[stage], kc,
                              (int)row0, pol);
             tma_load_2d_hint(sB_lo(stage), &d->tm_lo, &full[stage], kc,
@@ -225,9 +225,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t dAH = kmajor_desc<64>(aH + off);
             const uint64_t dBH = kmajor_desc<64>(bH + off);
             umma_f16(d_tmem, dAH, dBH, idesc, (first && ks == 0) ? 0u : 1u);
-            if (nprod == 3) {
+            if (nprod >= 3) {
               umma_f16(d_tmem, dAH, kmajor_desc<64>(bL + off), idesc, 1u);
               umma_f16(d_tmem, kmajor_desc<64>(aL + off), dBH, idesc, 1u);
+              if (nprod == 4)
+                umma_f16(d_tmem, kmajor_desc<64>(aL + off),
+                         kmajor_desc<64>(bL + off), idesc, 1u);
             }
           }
           umma_commit(&empty[stage]);
@@ -350,7 +353,9 @@ bool build_plan(Plan* P) {
     d.n = Z->n;
     d.m = tc_super_count(Z->n);
     d.nkb = (int)(Z->lpad / kKB);
-    d.nprod = Z->prec == PCC_PREC_BF16X1 ? 1 : 3;
+    d.nprod = Z->prec == PCC_PREC_BF16X1   ? 1
+              : Z->prec == PCC_PREC_BF16X4 ? 4
+                                           : 3;
     d.kalt = (Z->lpad > tc_tuning().kalt_min_l && d.nkb >= 2) ? 1 : 0;
     d.idesc = make_idesc_f16(Z->prec != PCC_PREC_FP16X3S, kBM, kBN);
     d.scale = (float)ldexp(1.0, -2 * Z->scale_exp);

@@ -5,8 +5,8 @@
 // Precision: z = hi + lo (two 16-bit halves, written by the variable
 // transformation).  Per tile the MMAs accumulate, in FP32 in TMEM,
 //     hi_Y hi_X^T + hi_Y lo_X^T + lo_Y hi_X^T          (3 products)
-// which recovers z_Y z_X^T up to the dropped lo lo^T term; BF16X1 runs the
-// first product only.
+// which recovers z_Y z_X^T up to the dropped lo lo^T term; BF16X4 adds
+// that fourth product, BF16X1 runs the first product only.
 //
 // Work decomposition (pcc_sched.h): 256 x 256 super-tiles of the upper
 // triangle in banded order, each split into two units of 128 rows x 256
@@ -323,11 +323,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t dAH = kmajor_desc<C::kSwz>(aH + off);
             const uint64_t dBH = kmajor_desc<C::kSwz>(bH + off);
             umma_f16(d_tmem, dAH, dBH, kIdesc, (first && ks == 0) ? 0u : 1u);
-            if (NPROD == 3) {
+            if (NPROD >= 3) {
               const uint64_t dAL = kmajor_desc<C::kSwz>(aL + off);
               const uint64_t dBL = kmajor_desc<C::kSwz>(bL + off);
               umma_f16(d_tmem, dAH, dBL, kIdesc, 1u);
               umma_f16(d_tmem, dAL, dBH, kIdesc, 1u);
+              if (NPROD == 4) umma_f16(d_tmem, dAL, dBL, kIdesc, 1u);
             }
           }
           if constexpr (CL == 1)
@@ -499,6 +500,9 @@ cudaError_t launch_kb(const pcc_zmat* Z, const pcc_zmat* ZB, TcParams& p,
     case PCC_PREC_FP16X3S:
       return launch_prec<3, false, KB, CROSS>(Z, ZB, p, grid, write_r,
                                               edges_on, s);
+    case PCC_PREC_BF16X4:
+      return launch_prec<4, true, KB, CROSS>(Z, ZB, p, grid, write_r,
+                                             edges_on, s);
     case PCC_PREC_BF16X1:
       return launch_prec<1, true, KB, CROSS>(Z, ZB, p, grid, write_r,
                                              edges_on, s);

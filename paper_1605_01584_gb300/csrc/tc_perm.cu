@@ -76,6 +76,7 @@ struct PermParams {
   int chunk;          // permutations per chunk
   int kbatch;         // permutations in this batch (workspace depth)
   int nkb;            // K blocks of 32
+  int lolo;           // 1: the fourth product lo.lo (BF16X4)
   const uint8_t* flags;
   uint32_t* counts;
   int* status;
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               umma_f16(d_tmem, dAH, dBH, idesc, (kb | ks) != 0);
               umma_f16(d_tmem, dAH, dBL, idesc, 1u);
               umma_f16(d_tmem, dAL, dBH, idesc, 1u);
+              if (p.lolo) umma_f16(d_tmem, dAL, dBL, idesc, 1u);
             }
             umma_commit(&empty[stage]);
             if (++stage == S) {
@@ -519,7 +521,8 @@ size_t perm_ws_budget() {
 pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                      int32_t k0, int32_t k1, uint32_t* d_counts,
                      cudaStream_t s) {
-  if (Z->prec != PCC_PREC_BF16X3 && Z->prec != PCC_PREC_FP16X3S)
+  if (Z->prec != PCC_PREC_BF16X3 && Z->prec != PCC_PREC_FP16X3S &&
+      Z->prec != PCC_PREC_BF16X4)
     return PCC_ERR_INVALID_ARG;
   const int64_t n = Z->n, lpad = Z->lpad;
   const size_t per_k = (size_t)n * (size_t)lpad * 2 * 2;  // hi + lo
@@ -542,7 +545,7 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     Z->perm_ws_bytes = need;
   }
   uint16_t* wh = static_cast<uint16_t*>(Z->perm_ws);
-  const bool bf16 = Z->prec == PCC_PREC_BF16X3;
+  const bool bf16 = Z->prec != PCC_PREC_FP16X3S;
   const int64_t m = (n + kPT - 1) / kPT;
   const int64_t tiles = m * (m + 1) / 2;
   const int sms = num_sms(Z->device);
@@ -589,6 +592,7 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     p.chunk = (int)chunk;
     p.kbatch = (int)kbatch;
     p.nkb = (int)(lpad / kPK);
+    p.lolo = Z->prec == PCC_PREC_BF16X4 ? 1 : 0;
     p.flags = Z->flags;
     p.counts = d_counts;
     p.status = Z->status;

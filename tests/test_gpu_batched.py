@@ -17,7 +17,7 @@ def _torch():
 
 SHAPES = [(3, 5, "fp16x3s"), (200, 2, "bf16x3"), (513, 33, "fp16x3s"),
           (300, 300, "bf16x3"), (1000, 64, "bf16x1"), (2049, 129, "fp16x3s"),
-          (130, 1000, "fp16x3s")]
+          (130, 1000, "fp16x3s"), (700, 200, "bf16x4")]
 
 
 def _setup(pcc, shapes, seed0=900):

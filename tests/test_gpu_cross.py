@@ -14,7 +14,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 4e-6, "bf16x3": 1e-5, "fp16x3s": 1e-5,
-       "bf16x1": 2e-2}
+       "bf16x4": 1e-5, "bf16x1": 2e-2}
 SENT = 7.0
 
 
@@ -59,7 +59,7 @@ SHAPES = [(2, 3, 2), (5, 2, 7), (129, 300, 64), (300, 129, 33),
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "fp16x3s",
-                                  "bf16x1"])
+                                  "bf16x4", "bf16x1"])
 @pytest.mark.parametrize("nx,ny,l", SHAPES)
 def test_cross_parity(pcc_gpu, prec, nx, ny, l):
     X = _data(nx, l, 3000 + nx + l)

@@ -20,7 +20,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 4e-6, "bf16x3": 1e-5, "fp16x3s": 1e-5,
-       "bf16x1": 2e-2}
+       "bf16x4": 1e-5, "bf16x1": 2e-2}
 
 
 def _torch():
@@ -74,7 +74,7 @@ SHAPES = [(2, 2), (3, 5), (127, 33), (128, 64), (129, 65), (255, 31),
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "fp16x3s",
-                                  "bf16x1"])
+                                  "bf16x4", "bf16x1"])
 @pytest.mark.parametrize("n,l", SHAPES)
 def test_allpairs_parity(pcc_gpu, prec, n, l):
     X = _data(n, l, seed=1000 + 7 * n + l)
@@ -134,7 +134,8 @@ def test_standardize_forms(pcc_gpu):
         X = _data(n, l, seed=n + l)
         Zo, fo = oracle.standardize(X)
         Xd = torch.from_numpy(X).cuda()
-        for prec in ["fp64", "fp32", "bf16x3", "fp16x3s", "bf16x1"]:
+        for prec in ["fp64", "fp32", "bf16x3", "fp16x3s", "bf16x4",
+                     "bf16x1"]:
             Z = pcc_gpu.pcc_standardize(Xd, prec)
             info = Z.info()
             buf = Z.buffers()
@@ -159,7 +160,8 @@ def test_standardize_forms(pcc_gpu):
                     _copy_from_ptr(lo, buf["lo"])
                     z = z + lo.float().cpu().numpy().astype(np.float64)
                 z = z * 2.0 ** (-info["scale_exp"])
-                tol = {"bf16x3": 2e-5, "fp16x3s": 4e-7, "bf16x1": 4e-3}[prec]
+                tol = {"bf16x3": 2e-5, "fp16x3s": 4e-7, "bf16x4": 2e-5,
+                       "bf16x1": 4e-3}[prec]
             assert np.all(z[:, l:] == 0), prec
             err = np.max(np.abs(z[:, :l] - Zo))
             assert err <= tol, (prec, n, l, err)

@@ -50,7 +50,7 @@ def check_band(X, perms, got, I, J):
 
 @pytest.mark.parametrize("n,l", [(130, 16), (300, 33), (257, 64),
                                  (520, 200), (400, 256), (300, 300)])
-@pytest.mark.parametrize("prec", ["fp16x3s", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp16x3s", "bf16x3", "bf16x4"])
 def test_perm_counts_parity(pcc_gpu, n, l, prec):
     X = synth.counts_log(n, l, seed=n * 7 + l)
     X[n // 2] = 2.5  # flagged row: counts stay 0
