@@ -112,6 +112,8 @@ def load(path: str | None = None):
         "pcc_set_tuning": (_ST, [_I32, _I32, _I32, ctypes.c_double,
                                  ctypes.c_double]),
         "pcc_get_tuning": (_ST, [_P, _P, _P, _P, _P]),
+        "pcc_set_pair_mma": (_ST, [_I32]),
+        "pcc_get_pair_mma": (_I32, []),
         "pcc_num_pairs": (_I64, [_I64]),
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
         "pcc_pair_coords": (_ST, [_I64, _I64, _P, _P]),
@@ -410,10 +412,14 @@ def pcc_debug_drop_loads(enable: bool):
 
 
 def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,
-                   cost_c1=0.0):
+                   cost_c1=0.0, pair_mma=None):
+    """Zeros (and pair_mma=None) keep a value; pair_mma 1/0 selects the
+    2-SM MMA or the multicast form of the CTA pairs (pcc_set_pair_mma)."""
     _check(load().pcc_set_tuning(int(stage_k), int(cluster), int(band_rows),
                                  float(cost_c0), float(cost_c1)),
            "pcc_set_tuning")
+    if pair_mma is not None:
+        _check(load().pcc_set_pair_mma(int(pair_mma)), "pcc_set_pair_mma")
 
 
 def pcc_get_tuning() -> dict:
@@ -423,7 +429,8 @@ def pcc_get_tuning() -> dict:
                                  ctypes.byref(b), ctypes.byref(c0),
                                  ctypes.byref(c1)), "pcc_get_tuning")
     return dict(stage_k=k.value, cluster=c.value, band_rows=b.value,
-                cost_c0=c0.value, cost_c1=c1.value)
+                cost_c0=c0.value, cost_c1=c1.value,
+                pair_mma=int(load().pcc_get_pair_mma()))
 
 
 def pcc_num_pairs(n: int) -> int:

@@ -4,6 +4,8 @@ The knobs never change results, only speed:
   stage_k    K per shared-memory ring stage (32: 4 stages, 64: 2 stages)
   cluster    2 = CTA pairs sharing the column operand by TMA multicast,
              1 = independent CTAs
+  pair_mma   with CTA pairs and stage_k 32: 1 = one 2-SM MMA per pair
+             (each CTA loads half of the column operand), 0 = multicast
   band_rows  super-tile rows per band of the pair schedule
 and the batched work split's cost model (cycles per unit c0, per K block and
 product c1).
@@ -30,6 +32,7 @@ from . import (PccError, load, pcc_allpairs_upper, pcc_get_tuning,
 DEFAULT_CANDIDATES = {
     "stage_k": (32, 64),
     "cluster": (2, 1),
+    "pair_mma": (1, 0),
     "band_rows": (16, 32, 64),
 }
 
@@ -94,7 +97,7 @@ def apply(n: int, l: int, prec: str, cache: dict | None = None) -> bool:
     if not b:
         return False
     pcc_set_tuning(stage_k=b["stage_k"], cluster=b["cluster"],
-                   band_rows=b["band_rows"])
+                   band_rows=b["band_rows"], pair_mma=b.get("pair_mma"))
     return True
 
 
@@ -131,15 +134,19 @@ def tune_pairs(n: int, l: int, prec: str = "auto", candidates=None,
     before = pcc_get_tuning()
     results = []
     try:
-        for sk, cl, bd in itertools.product(cand["stage_k"], cand["cluster"],
-                                            cand["band_rows"]):
-            pcc_set_tuning(stage_k=sk, cluster=cl, band_rows=bd)
+        for sk, cl, pm, bd in itertools.product(
+                cand["stage_k"], cand["cluster"], cand["pair_mma"],
+                cand["band_rows"]):
+            # the pair form only differs for CTA pairs with K = 32 stages
+            if pm != cand["pair_mma"][0] and not (cl == 2 and sk == 32):
+                continue
+            pcc_set_tuning(stage_k=sk, cluster=cl, band_rows=bd, pair_mma=pm)
             ms = _time_ms(lambda: pcc_allpairs_upper(Z, R), reps)
-            results.append({"stage_k": sk, "cluster": cl, "band_rows": bd,
-                            "ms": ms})
+            results.append({"stage_k": sk, "cluster": cl, "pair_mma": pm,
+                            "band_rows": bd, "ms": ms})
     finally:
         pcc_set_tuning(before["stage_k"], before["cluster"],
-                       before["band_rows"])
+                       before["band_rows"], pair_mma=before["pair_mma"])
     best = min(results, key=lambda r: r["ms"])
     entry = {"n": n, "l": l, "prec": resolved, "best": best,
              "all": results}

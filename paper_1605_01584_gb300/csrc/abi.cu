@@ -108,6 +108,8 @@ TcTuning g_tune = [] {
   t.stage_k = (e && atoi(e) == 64) ? 64 : 32;
   e = getenv("PCC_TC_CLUSTER");
   t.cluster = (e && atoi(e) == 1) ? 1 : 2;
+  e = getenv("PCC_TC_PAIR");
+  t.pair_mma = (e && atoi(e) == 0) ? 0 : 1;
   e = getenv("PCC_TC_BAND");
   const int v = e ? atoi(e) : 0;
   t.band = (v >= 1 && v <= 4096) ? v : 32;
@@ -501,6 +503,16 @@ pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
   tc_set_tuning(t);
   return PCC_OK;
 }
+
+pcc_status pcc_set_pair_mma(int32_t on) {
+  if (on != 0 && on != 1) return PCC_ERR_INVALID_ARG;
+  TcTuning t = tc_tuning();
+  t.pair_mma = on;
+  tc_set_tuning(t);
+  return PCC_OK;
+}
+
+int32_t pcc_get_pair_mma(void) { return tc_tuning().pair_mma; }
 
 pcc_status pcc_get_tuning(int32_t* stage_k, int32_t* cluster,
                           int32_t* band_rows, double* cost_c0,

@@ -65,6 +65,8 @@ bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
 struct TcTuning {
   int stage_k;       // K per ring stage: 32 or 64
   int cluster;       // 2 = CTA pairs sharing B by multicast, 1 = single CTAs
+  int pair_mma;      // with cluster 2: the pair runs one 2-SM MMA (M = 256)
+                     // and each CTA loads only its half of B
   int64_t band;      // super-tile rows per band of the pair schedule
   double cost_c0;    // batched plan: cycles per unit outside the K loop
   double cost_c1;    // batched plan: cycles per K block and product

@@ -14,9 +14,9 @@
 // Algorithm 1 strides thread groups over tile ids.
 //
 // CTA roles (320 threads):
-//   warp 0      TMA producer: per K block of 64, loads A = rows of the unit
-//               (hi, lo: 128 x 64 each) and B = its columns (hi, lo: 256 x
-//               64 each) into a ring of shared-memory stages (128-B swizzle).
+//   warp 0      TMA producer: per K block (32 or 64), loads A = rows of the
+//               unit (hi, lo: 128 rows each) and B = its columns (hi, lo:
+//               256 rows each) into a ring of shared-memory stages.
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32
 //               accumulators) and one elected thread issues the MMAs
 //               (M = 128, N = 256, K = 16 per instruction), committing each
@@ -38,12 +38,27 @@
 // epilogue writes a dense row-major R (pitch ldr).  Super-tiles are taken
 // in bands of G rows, column by column within a band (Eq. (7)-(8) with the
 // roles of rows and columns swapped, per band), so that a band's A rows
-// stay in L2 while B streams past them once.  By default the grid is made of 2-CTA clusters: the CTAs of a pair
-// compute the two halves of one super-tile, which need the same 256 B rows,
-// so each loads 128 of them and multicasts them to both (a third less L2 to
-// shared-memory traffic); both MMAs must release a stage before either
-// producer refills it.  Every wait is bounded (pcc_ptx.cuh): a wait that runs out records
-// PCC_ERR_TIMEOUT and the CTA drains its copies, frees TMEM and returns.
+// stay in L2 while B streams past them once.
+//
+// CTA pairs (the default: 2-CTA clusters).  The CTAs of a pair compute the
+// two halves of one super-tile, which need the same 256 B rows.
+//   PAIR (the default, K = 32 stages): the pair is one 2-SM MMA unit.  Each
+//     CTA loads its 128 A rows and 128 of the B rows into its own stage, and
+//     the even CTA issues tcgen05.mma.cta_group::2 with M = 256: the pair's
+//     tensor cores exchange the B halves, so each SM takes a third less
+//     operand data from L2 than with multicast, and a stage is a third
+//     smaller (six stages instead of four).  Both CTAs' copies count on the
+//     even CTA's stage barrier; its commits release the stage in both CTAs
+//     and hand each CTA its half of the accumulator; both epilogues release
+//     the accumulator to the even CTA.
+//   otherwise: each CTA runs its own M = 128 MMA; each loads 128 of the B
+//     rows and multicasts them to both, and both MMAs must release a stage
+//     before either producer refills it.
+// Measured at 65,536 x 512: 4.76 ms (2-SM MMA), 5.06 ms (multicast), 5.42
+// ms (independent CTAs); clusters of 4 to 8 CTAs sharing rows by multicast
+// were slower still.  Every wait is bounded (pcc_ptx.cuh): a wait that runs
+// out records PCC_ERR_TIMEOUT and the CTA drains its copies, frees TMEM and
+// returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -94,10 +109,12 @@ struct TcParams {
 // KB = K per ring stage: 64 (one 128-B swizzle row of 16-bit elements, 2
 // stages of 96 KB) or 32 (64-B swizzle, 4 stages of 48 KB: the same bytes in
 // flight, refilled at half the granularity).
-template <int NPROD, int KB>
+// PAIR (the 2-SM MMA of a CTA pair): each CTA holds only its 128 of the
+// 256 B rows, so a stage is a third smaller and the ring holds six.
+template <int NPROD, int KB, bool PAIR = false>
 struct Cfg {
   static constexpr int kTileA = kBM * KB * 2;
-  static constexpr int kTileB = kBN * KB * 2;
+  static constexpr int kTileB = (PAIR ? kBM : kBN) * KB * 2;
   static constexpr int kSwz = KB * 2;  // swizzle span in bytes
   static constexpr int kStageBytes =
       NPROD == 1 ? (kTileA + kTileB) : 2 * (kTileA + kTileB);
@@ -130,7 +147,7 @@ __device__ __forceinline__ void unit_coords(BandCursor* cur, const TcParams& p,
 }
 
 template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, int CL,
-          bool CROSS>
+          bool CROSS, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap tm_hi,
                const __grid_constant__ CUtensorMap tm_lo,
@@ -139,11 +156,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   // B operand maps: the second matrix's for CROSS, else Z's own
   const CUtensorMap* mb_hi = CROSS ? &tmb_hi : &tm_hi;
   const CUtensorMap* mb_lo = CROSS ? &tmb_lo : &tm_lo;
-  using C = Cfg<NPROD, KB>;
+  static_assert(!PAIR || CL == 2, "the 2-SM MMA runs on CTA pairs");
+  using C = Cfg<NPROD, KB, PAIR>;
   constexpr int kTileA = C::kTileA;
   constexpr int kTileB = C::kTileB;
   constexpr int S = C::kStages;
-  constexpr uint32_t kIdesc = make_idesc_f16(BF16, kBM, kBN);
+  // PAIR: one instruction covers the pair's 256 rows
+  constexpr uint32_t kIdesc = make_idesc_f16(BF16, PAIR ? 2 * kBM : kBM, kBN);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -175,11 +194,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);  // released by the MMA of every CTA
+      // released by the MMA of every CTA (PAIR: by the one pair MMA)
+      mbar_init(&empty[s], PAIR ? 1 : CL);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kEpiWarps);
+      // PAIR: the even CTA's accumulator barriers count both epilogues
+      mbar_init(&tempty[a], PAIR ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(mdone, 1);
     *abort_flag = 0;
@@ -194,8 +215,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, 512);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(tmem_holder, 512);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_holder, 512);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -232,8 +258,30 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
           const int kc = kb * KB;
+          if constexpr (PAIR) {
+            // each CTA loads its 128 A rows and its 128 of the 256 B rows
+            // into its own stage; the even CTA's barrier counts the bytes
+            // of both, since its one MMA reads both stages
+            if (crank == 0)
+              mbar_arrive_expect_tx(&full[stage], 2 * C::kStageBytes);
+            const uint32_t fb = cluster_addr(&full[stage], 0);
+            const int brow = (int)(col0 + crank * kBM);
+            tma_load_2d_pair(sA_hi(stage), &tm_hi, fb, kc, (int)row0, pol);
+            tma_load_2d_pair(sB_hi(stage), mb_hi, fb, kc, brow, pol);
+            if (NPROD > 1) {
+              tma_load_2d_pair(sA_lo(stage), &tm_lo, fb, kc, (int)row0, pol);
+              tma_load_2d_pair(sB_lo(stage), mb_lo, fb, kc, brow, pol);
+            }
+            issued_mask |= 1u << stage;
+            last_phase[stage] = phase;
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            continue;
+          }
+          mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
           // Z is re-read by many tiles: keep it in L2 ahead of the
           // evict-first output stream
           tma_load_2d_hint(sA_hi(stage), &tm_hi, &full[stage], kc, (int)row0,
@@ -273,16 +321,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
       }
-      // drain: every issued copy must land before the CTA may exit
+      // drain: every issued copy must land before the CTA may exit (PAIR:
+      // the even CTA's barriers also count the odd CTA's copies)
       WaitCtx wd = w;
       volatile int never = 0;
       wd.abort_flag = &never;
-      for (int s = 0; s < S; ++s)
-        if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
+      if (!PAIR || crank == 0)
+        for (int s = 0; s < S; ++s)
+          if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------- MMA issuer
-    if (lane == 0) {
+    // (PAIR: the even CTA issues for both)
+    if (lane == 0 && (!PAIR || crank == 0)) {
       BandCursor cur;
       band_cursor_init(&cur, p.m, p.G);
       int stage = 0;
@@ -322,16 +373,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t off = ks * kUK * 2;  // bytes along K
             const uint64_t dAH = kmajor_desc<C::kSwz>(aH + off);
             const uint64_t dBH = kmajor_desc<C::kSwz>(bH + off);
-            umma_f16(d_tmem, dAH, dBH, kIdesc, (first && ks == 0) ? 0u : 1u);
+            auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
+              if constexpr (PAIR)
+                umma_f16_pair(d_tmem, a, b, kIdesc, acc_in);
+              else
+                umma_f16(d_tmem, a, b, kIdesc, acc_in);
+            };
+            mma(dAH, dBH, (first && ks == 0) ? 0u : 1u);
             if (NPROD >= 3) {
               const uint64_t dAL = kmajor_desc<C::kSwz>(aL + off);
               const uint64_t dBL = kmajor_desc<C::kSwz>(bL + off);
-              umma_f16(d_tmem, dAH, dBL, kIdesc, 1u);
-              umma_f16(d_tmem, dAL, dBH, kIdesc, 1u);
-              if (NPROD == 4) umma_f16(d_tmem, dAL, dBL, kIdesc, 1u);
+              mma(dAH, dBL, 1u);
+              mma(dAL, dBH, 1u);
+              if (NPROD == 4) mma(dAL, dBL, 1u);
             }
           }
-          if constexpr (CL == 1)
+          if constexpr (PAIR)
+            umma_commit_pair(&empty[stage], 3);  // frees the stage in both
+          else if constexpr (CL == 1)
             umma_commit(&empty[stage]);
           else
             umma_commit_mc(&empty[stage], 3);  // frees the stage in both
@@ -341,13 +400,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!ok) break;
-        umma_commit(&tfull[acc0]);
-        if (p.kalt) umma_commit(&tfull[acc]);
+        if constexpr (PAIR) {
+          // each CTA's epilogue reads its own half of the accumulator
+          umma_commit_pair(&tfull[acc0], 3);
+          if (p.kalt) umma_commit_pair(&tfull[acc], 3);
+        } else {
+          umma_commit(&tfull[acc0]);
+          if (p.kalt) umma_commit(&tfull[acc]);
+        }
         acc ^= 1;
         if (acc == 0) aphase ^= 1u;
       }
       // all MMAs issued by this thread complete before TMEM is released
-      umma_commit(mdone);
+      if constexpr (PAIR)
+        umma_commit_pair(mdone, 1);
+      else
+        umma_commit(mdone);
       WaitCtx wd = w;
       volatile int never = 0;
       wd.abort_flag = &never;
@@ -409,8 +477,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&tempty[acc0]);
-        if (p.kalt) mbar_arrive(&tempty[acc]);
+        if (PAIR && crank != 0) {
+          // the accumulator is released to the even CTA's MMA issuer
+          mbar_arrive_cluster(cluster_addr(&tempty[acc0], 0));
+          if (p.kalt) mbar_arrive_cluster(cluster_addr(&tempty[acc], 0));
+        } else {
+          mbar_arrive(&tempty[acc0]);
+          if (p.kalt) mbar_arrive(&tempty[acc]);
+        }
       }
       acc ^= 1;
       if (acc == 0) aphase ^= 1u;
@@ -420,25 +494,45 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if constexpr (PAIR) {
+    // after an abort, the odd CTA's last copies are counted on barriers no
+    // one waits for any more: give them time to land (bounded, error path)
+    if (*abort_flag && threadIdx.x == 0) {
+      const uint64_t t0 = global_timer_ns();
+      while (global_timer_ns() - t0 < 200000u) {
+      }
+    }
+    __syncthreads();
+  }
   // neither CTA leaves while the other may still write its shared memory
   if constexpr (CL == 2) cluster_sync();
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem_base, 512);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem_base, 512);
+    else
+      tmem_dealloc(tmem_base, 512);
   }
 }
 
 template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, bool CROSS>
 cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
                         const TcParams& p, int grid, cudaStream_t s) {
-  const int smem = Cfg<NPROD, KB>::kSmemBytes;
   const CUtensorMap& th = KB == 64 ? Z->tm_hi : Z->tm_hi32;
   const CUtensorMap& tl = KB == 64 ? Z->tm_lo : Z->tm_lo32;
   const CUtensorMap& tbh = KB == 64 ? ZB->tm_hi : ZB->tm_hi32;
   const CUtensorMap& tbl = KB == 64 ? ZB->tm_lo : ZB->tm_lo32;
   const int64_t tiles = (p.u_end - p.u_begin) / 2;
   if (tc_tuning().cluster == 2 && tiles >= 2) {
-    auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2, CROSS>;
+    // the 2-SM MMA form exists for K = 32 stages
+    constexpr bool kPairOk = KB == 32;
+    const bool pair = kPairOk && tc_tuning().pair_mma != 0;
+    auto fn = pair ? k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2, CROSS,
+                                kPairOk>
+                   : k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2, CROSS,
+                                false>;
+    const int smem = pair ? Cfg<NPROD, KB, kPairOk>::kSmemBytes
+                          : Cfg<NPROD, KB, false>::kSmemBytes;
     cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -452,7 +546,8 @@ cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int max_clusters = 0;  // per template instance
+    static int max_clusters_of[2] = {0, 0};  // per form, per instance
+    int& max_clusters = max_clusters_of[pair ? 1 : 0];
     if (max_clusters == 0) {
       cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
       int mc = 0;
@@ -469,7 +564,8 @@ cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 1, CROSS>;
+  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 1, CROSS, false>;
+  const int smem = Cfg<NPROD, KB, false>::kSmemBytes;
   cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, kThreads, smem, s>>>(th, tl, tbh, tbl, p);

@@ -33,7 +33,9 @@ def test_tune_small_shape_and_apply(pcc_gpu, tmp_path):
     before = pcc.pcc_get_tuning()
     e = autotune.tune_pairs(2048, 128, "bf16x3", reps=2, path=p,
                             candidates={"band_rows": (8, 32)})
-    assert len(e["all"]) == 8 and e["best"]["ms"] > 0
+    # 2 x 2 x 2 stage/cluster/band combinations, plus the multicast pair
+    # form for the two with CTA pairs and K = 32 stages
+    assert len(e["all"]) == 10 and e["best"]["ms"] > 0
     assert pcc.pcc_get_tuning() == before  # tuning run restores the knobs
     X = torch.rand((2048, 128), device="cuda")
     Z = pcc.pcc_standardize(X, "bf16x3")
@@ -48,4 +50,4 @@ def test_tune_small_shape_and_apply(pcc_gpu, tmp_path):
         assert torch.equal(R0, R1)  # knobs never change results
     finally:
         pcc.pcc_set_tuning(before["stage_k"], before["cluster"],
-                           before["band_rows"])
+                           before["band_rows"], pair_mma=before["pair_mma"])

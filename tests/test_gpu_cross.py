@@ -78,8 +78,8 @@ def test_cross_pitch_leaves_gap_untouched(pcc_gpu, prec):
     _compare(got[:, :270], oracle.cross_rows(X, Y), TOL[prec], prec)
 
 
-@pytest.mark.parametrize("cluster", [1, 2])
-def test_cross_self_matches_triangle_bits(pcc_gpu, cluster):
+@pytest.mark.parametrize("cluster,pair", [(1, 0), (2, 0), (2, 1)])
+def test_cross_self_matches_triangle_bits(pcc_gpu, cluster, pair):
     """cross(Z, Z) is the full square: its strict upper part is the packed
     triangle bit for bit (same operand roles, same K order, same epilogue
     arithmetic), its lower part the transpose within 1e-5, and the diagonal
@@ -90,8 +90,8 @@ def test_cross_self_matches_triangle_bits(pcc_gpu, cluster):
     on each of its 30 updates at l = 130: 1.9e-5 (measured: 1.5e-5)."""
     import torch
     pcc = pcc_gpu
-    old = pcc.pcc_get_tuning()["cluster"]
-    pcc.pcc_set_tuning(cluster=cluster)
+    old = pcc.pcc_get_tuning()
+    pcc.pcc_set_tuning(cluster=cluster, pair_mma=pair)
     try:
         X = _data(600, 130, 13)
         Xd = torch.from_numpy(X).cuda()
@@ -105,7 +105,7 @@ def test_cross_self_matches_triangle_bits(pcc_gpu, cluster):
         R = R.cpu().numpy()
         P = P.cpu().numpy()
     finally:
-        pcc.pcc_set_tuning(cluster=old)
+        pcc.pcc_set_tuning(cluster=old["cluster"], pair_mma=old["pair_mma"])
     I, J = np.triu_indices(n, 1)
     up = R[I, J]
     assert np.array_equal(np.isnan(up), np.isnan(P))

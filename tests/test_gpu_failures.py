@@ -9,8 +9,8 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cluster", [2, 1])
-def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster):
+@pytest.mark.parametrize("cluster,pair", [(2, 1), (2, 0), (1, 0)])
+def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster, pair):
     import torch
     pcc = pcc_gpu
     X = torch.from_numpy(synth.counts_log(1200, 64, 31)).cuda()
@@ -18,7 +18,7 @@ def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster):
     n = 1200
     R = torch.full((n * (n - 1) // 2,), 7.0, device="cuda")
     before = pcc.pcc_get_tuning()
-    pcc.pcc_set_tuning(cluster=cluster)
+    pcc.pcc_set_tuning(cluster=cluster, pair_mma=pair)
     try:
         pcc.pcc_set_wait_limit_ns(200_000_000)  # 0.2 s
         pcc.pcc_debug_drop_loads(True)
@@ -27,7 +27,8 @@ def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster):
     finally:
         pcc.pcc_debug_drop_loads(False)
         pcc.pcc_set_wait_limit_ns(4_000_000_000)
-        pcc.pcc_set_tuning(cluster=before["cluster"])
+        pcc.pcc_set_tuning(cluster=before["cluster"],
+                           pair_mma=before["pair_mma"])
     # the status word was cleared by the read and the context still works
     assert pcc.pcc_sync_status(Z) == 0
     pcc.pcc_allpairs_upper(Z, R)
