@@ -315,15 +315,20 @@ pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
 pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
                           double cost_c0, double cost_c1);
 
-/* The CTA-pair form of the tensor-core pair kernels (cluster = 2 with
- * stage_k = 32).  on = 1 (the default; PCC_TC_PAIR=0 in the environment
- * selects 0 when the library loads): the two CTAs of a pair run one 2-SM
- * MMA (tcgen05.mma.cta_group::2, M = 256 rows over both), each CTA loading
- * only its 128 of the tile's 256 column rows, which the pair's tensor cores
- * exchange.  on = 0: each CTA runs its own M = 128 MMA and the column rows
- * reach both CTAs by TMA multicast.  Affects later launches only; the
- * result is the same.  Errors: PCC_ERR_INVALID_ARG unless on is 0 or 1.
- * The paper has no counterpart (a GB300 execution choice). */
+/* The CTA-pair form of the tensor-core kernels.  on = 1 (the default;
+ * PCC_TC_PAIR=0 in the environment selects 0 when the library loads): two
+ * CTAs run one 2-SM MMA (tcgen05.mma.cta_group::2, M = 256 rows over both),
+ * each loading only half of the column operand, which the pair's tensor
+ * cores exchange.
+ *   pcc_allpairs_upper / _edges / cross (cluster = 2, stage_k = 32): the
+ *   pair computes one 256 x 256 super-tile; on = 0: each CTA runs its own
+ *   M = 128 MMA and the column rows reach both CTAs by TMA multicast.
+ *   pcc_perm_test: the pair computes two 128 x 128 tiles of one tile
+ *   column, each CTA loading one of the two permutations of a pass; on = 0:
+ *   independent CTAs, one tile each.
+ * Affects later launches only; the results are the same.  Errors:
+ * PCC_ERR_INVALID_ARG unless on is 0 or 1.  The paper has no counterpart
+ * (a GB300 execution choice). */
 pcc_status pcc_set_pair_mma(int32_t on);
 int32_t pcc_get_pair_mma(void);
 

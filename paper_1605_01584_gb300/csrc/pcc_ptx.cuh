@@ -270,6 +270,22 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst,
       : "memory");
 }
 
+// 3-D tiled load, completion counted on an mbarrier of either CTA of the
+// pair (shared::cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(void* dst,
+                                                 const CUtensorMap* m,
+                                                 uint32_t bar_cluster,
+                                                 int32_t c0, int32_t c1,
+                                                 int32_t c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_"
+      "tx::bytes.cta_group::2 [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(bar_cluster), "r"(c0), "r"(c1),
+      "r"(c2)
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem,
                                                 uint32_t ncols) {
   asm volatile(

@@ -49,7 +49,6 @@ constexpr int kPThreads = 320;
 constexpr int kPEpiWarps = 8;
 constexpr int kPTile = kPT * kPK * 2;        // 8 KB: 128 rows x 32 (16-bit)
 constexpr int kPBHalf = 2 * kPTile;          // B hi (or lo): 256 rows, 16 KB
-constexpr int kPStageB = 2 * kPBHalf;        // B hi + lo of two permutations
 constexpr int kPAcc = 2 * kPT;               // TMEM columns per accumulator
 constexpr int kPMaxResidentK = 256;          // resident A up to lpad 256
 constexpr int kPSmemBudget = 232448;
@@ -68,10 +67,28 @@ __device__ __forceinline__ void col_tri_coords(int64_t t, int64_t* y,
   *y = t - xx * (xx + 1) / 2;
 }
 
+// PAIR items: the tiles of column x of the triangle taken two by two, rows
+// (2r, 2r+1); column x holds floor((x+2)/2) pairs (the last one alone when
+// x is even) and Q(x) = floor((x+1)/2) * floor((x+2)/2) pairs come before
+// it.  The closed-form estimate is corrected by exact integer tests.
+__host__ __device__ __forceinline__ int64_t col_pairs_before(int64_t x) {
+  return ((x + 1) / 2) * ((x + 2) / 2);
+}
+
+__device__ __forceinline__ void col_pair_coords(int64_t t, int64_t* r,
+                                                int64_t* x) {
+  int64_t xx = (int64_t)(2.0 * sqrt((double)t));
+  if (xx < 0) xx = 0;
+  while (xx > 0 && col_pairs_before(xx) > t) --xx;
+  while (col_pairs_before(xx + 1) <= t) ++xx;
+  *x = xx;
+  *r = t - col_pairs_before(xx);
+}
+
 struct PermParams {
   int64_t n;
   int64_t m;          // 128-wide tiles per side
-  int64_t items;      // tiles * nchunks
+  int64_t items;      // tiles (PAIR: tile pairs) * nchunks
   int nchunks;        // permutation chunks per tile
   int chunk;          // permutations per chunk
   int kbatch;         // permutations in this batch (workspace depth)
@@ -83,13 +100,18 @@ struct PermParams {
   uint64_t wait_ns;
 };
 
-template <bool RESA>
+// PAIR: a CTA pair runs one 2-SM MMA (M = 256: the two CTAs' tiles); each
+// CTA holds the 128 B rows of one permutation, so its B stages are half as
+// large.
+template <bool RESA, bool PAIR = false>
 struct PCfg {
   // resident A: nkb blocks x (hi + lo) tiles, at most kPMaxResidentK / kPK
   static constexpr int kABytes = RESA ? (kPMaxResidentK / kPK) * 2 * kPTile : 0;
-  // stage: [B hi | B lo], 256 rows each (two permutations), streamed A in
-  // front of them
-  static constexpr int kStageBytes = RESA ? kPStageB : 2 * kPTile + kPStageB;
+  // B hi (or lo) rows of a stage: 256 (two permutations), PAIR: 128 (one)
+  static constexpr int kBHalf = PAIR ? kPTile : kPBHalf;
+  // stage: [B hi | B lo], streamed A in front of them
+  static constexpr int kStageBytes =
+      RESA ? 2 * kBHalf : 2 * kPTile + 2 * kBHalf;
   static constexpr int kBarBytes = 256;
   static constexpr int kStages =
       (kPSmemBudget - 1024 - kABytes - kBarBytes) / kStageBytes > 8
@@ -101,13 +123,17 @@ struct PCfg {
 };
 
 // One block per (permutation, group of rows).  The permutation is checked
-// and staged in shared memory; each warp then takes one row at a time,
-// copies its hi and lo halves into shared memory with 16-byte loads, and
-// every lane writes 8 permuted elements of each half with one 16-byte
-// store (lpad is a multiple of 64, so rows split into whole 8-element
-// groups).  Shared memory: 4 * lpad bytes of indices and 4 * lpad per warp.
+// and staged in shared memory; with NG > 0 each lane then keeps the indices
+// of its NG groups of 8 outputs in registers for all the block's rows (rows
+// up to 256 * NG samples).  Each warp takes one row at a time and stages it
+// in shared memory with hi and lo interleaved (word s = hi[s] | lo[s] << 16),
+// so one 4-byte read fetches both halves of a sample; every lane then
+// writes 8 permuted elements of each half with one 16-byte store per half
+// (lpad is a multiple of 64, so rows split into whole 8-element groups).
+// Shared memory: 4 * lpad bytes of indices and 4 * lpad per warp.
 constexpr int kGatherWarps = 8;
 
+template <int NG>
 __global__ void __launch_bounds__(kGatherWarps * 32)
     k_perm_gather(const uint16_t* __restrict__ hi,
                   const uint16_t* __restrict__ lo,
@@ -117,9 +143,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
                   int* __restrict__ status) {
   extern __shared__ uint8_t gsm[];
   int32_t* pi = reinterpret_cast<int32_t*>(gsm);              // lpad
-  uint16_t* rows = reinterpret_cast<uint16_t*>(pi + lpad);    // per warp
+  uint32_t* rows = reinterpret_cast<uint32_t*>(pi + lpad);    // per warp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t kk = blockIdx.y;
+  const int64_t ngroups = lpad / 8;
   const int32_t* src = perms + (k_lo + kk) * l;
   bool bad = false;
   for (int64_t s = threadIdx.x; s < lpad; s += blockDim.x) {
@@ -132,56 +159,108 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
   }
   if (bad) atomicCAS(status, 0, (int)PCC_ERR_INVALID_ARG);
   __syncthreads();
-  uint16_t* wrow = rows + (size_t)warp * 2 * lpad;  // hi | lo of one row
+  // this lane's indices: groups v = lane + 32 g
+  int32_t idx[NG > 0 ? 8 * NG : 1];
+  if constexpr (NG > 0) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int64_t v = lane + 32 * g;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) idx[8 * g + t] = v < ngroups ? pi[v * 8 + t] : -1;
+    }
+  }
+  uint32_t* wrow = rows + (size_t)warp * lpad;  // one row, hi | lo << 16
   const int64_t j0 = blockIdx.x * rows_per_block;
   const int64_t j1 = j0 + rows_per_block < n ? j0 + rows_per_block : n;
   for (int64_t j = j0 + warp; j < j1; j += kGatherWarps) {
     const uint4* gh = reinterpret_cast<const uint4*>(hi + j * lpad);
     const uint4* gl = reinterpret_cast<const uint4*>(lo + j * lpad);
-    uint4* sh = reinterpret_cast<uint4*>(wrow);
-    uint4* sl = reinterpret_cast<uint4*>(wrow + lpad);
-    for (int64_t v = lane; v < lpad / 8; v += 32) {
-      sh[v] = gh[v];
-      sl[v] = gl[v];
+    uint4* sw = reinterpret_cast<uint4*>(wrow);
+    for (int64_t v = lane; v < ngroups; v += 32) {
+      const uint4 a = gh[v], b = gl[v];  // samples 8v .. 8v+7
+      uint4 w0, w1;
+      w0.x = (a.x & 0xFFFFu) | (b.x << 16);
+      w0.y = (a.x >> 16) | (b.x & 0xFFFF0000u);
+      w0.z = (a.y & 0xFFFFu) | (b.y << 16);
+      w0.w = (a.y >> 16) | (b.y & 0xFFFF0000u);
+      w1.x = (a.z & 0xFFFFu) | (b.z << 16);
+      w1.y = (a.z >> 16) | (b.z & 0xFFFF0000u);
+      w1.z = (a.w & 0xFFFFu) | (b.w << 16);
+      w1.w = (a.w >> 16) | (b.w & 0xFFFF0000u);
+      sw[2 * v] = w0;
+      sw[2 * v + 1] = w1;
     }
     __syncwarp();
     uint4* oh = reinterpret_cast<uint4*>(ohi + (kk * n + j) * lpad);
     uint4* ol = reinterpret_cast<uint4*>(olo + (kk * n + j) * lpad);
-    for (int64_t v = lane; v < lpad / 8; v += 32) {
-      uint16_t a[8], b[8];
+    auto emit = [&](int64_t v, const int32_t* q) {
+      uint32_t wv[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int32_t q = pi[v * 8 + t];
-        a[t] = q >= 0 ? wrow[q] : (uint16_t)0;
-        b[t] = q >= 0 ? wrow[lpad + q] : (uint16_t)0;
-      }
-      uint4 ua, ub;
-      ua.x = a[0] | ((uint32_t)a[1] << 16);
-      ua.y = a[2] | ((uint32_t)a[3] << 16);
-      ua.z = a[4] | ((uint32_t)a[5] << 16);
-      ua.w = a[6] | ((uint32_t)a[7] << 16);
-      ub.x = b[0] | ((uint32_t)b[1] << 16);
-      ub.y = b[2] | ((uint32_t)b[3] << 16);
-      ub.z = b[4] | ((uint32_t)b[5] << 16);
-      ub.w = b[6] | ((uint32_t)b[7] << 16);
+      for (int t = 0; t < 8; ++t) wv[t] = q[t] >= 0 ? wrow[q[t]] : 0u;
+      uint4 ua, ub;  // hi: low halves, lo: high halves
+      ua.x = (wv[0] & 0xFFFFu) | (wv[1] << 16);
+      ua.y = (wv[2] & 0xFFFFu) | (wv[3] << 16);
+      ua.z = (wv[4] & 0xFFFFu) | (wv[5] << 16);
+      ua.w = (wv[6] & 0xFFFFu) | (wv[7] << 16);
+      ub.x = (wv[0] >> 16) | (wv[1] & 0xFFFF0000u);
+      ub.y = (wv[2] >> 16) | (wv[3] & 0xFFFF0000u);
+      ub.z = (wv[4] >> 16) | (wv[5] & 0xFFFF0000u);
+      ub.w = (wv[6] >> 16) | (wv[7] & 0xFFFF0000u);
       oh[v] = ua;
       ol[v] = ub;
+    };
+    if constexpr (NG > 0) {
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const int64_t v = lane + 32 * g;
+        if (v < ngroups) emit(v, idx + 8 * g);
+      }
+    } else {
+      for (int64_t v = lane; v < ngroups; v += 32) emit(v, pi + v * 8);
     }
     __syncwarp();
   }
 }
 
-template <bool BF16, bool RESA>
+// the gather for rows of lpad samples: indices in registers up to 1024
+cudaError_t launch_gather(dim3 g, size_t gsmem, cudaStream_t s,
+                          const uint16_t* hi, const uint16_t* lo,
+                          const int32_t* perms, int64_t n, int64_t l,
+                          int64_t lpad, int64_t k_lo, int64_t rpb,
+                          uint16_t* ohi, uint16_t* olo, int* status) {
+  const int64_t need = (lpad / 8 + 31) / 32;
+  auto go = [&](auto fn) {
+    if (gsmem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(
+          fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+      if (e != cudaSuccess) return e;
+    }
+    fn<<<g, kGatherWarps * 32, gsmem, s>>>(hi, lo, perms, n, l, lpad, k_lo,
+                                            rpb, ohi, olo, status);
+    return cudaGetLastError();
+  };
+  if (need <= 1) return go(k_perm_gather<1>);
+  if (need <= 2) return go(k_perm_gather<2>);
+  if (need <= 4) return go(k_perm_gather<4>);
+  return go(k_perm_gather<0>);
+}
+
+template <bool BF16, bool RESA, bool PAIR>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_perm_tc(const __grid_constant__ CUtensorMap tz_hi,
               const __grid_constant__ CUtensorMap tz_lo,
               const __grid_constant__ CUtensorMap tp_hi,
               const __grid_constant__ CUtensorMap tp_lo, const PermParams p) {
-  using C = PCfg<RESA>;
+  using C = PCfg<RESA, PAIR>;
   constexpr int S = C::kStages;
-  // N = 128: r_obs and a lone last permutation; N = 256: two permutations
-  constexpr uint32_t kIdesc1 = make_idesc_f16(BF16, kPT, kPT);
-  constexpr uint32_t kIdesc2 = make_idesc_f16(BF16, kPT, 2 * kPT);
+  // N = 128: r_obs and a lone last permutation; N = 256: two permutations.
+  // PAIR: always M = 256 (both CTAs' tiles) and N = 256 (one permutation's
+  // 128 B rows from each CTA; r_obs and a lone permutation repeat theirs)
+  constexpr uint32_t kIdesc1 =
+      PAIR ? make_idesc_f16(BF16, 2 * kPT, 2 * kPT)
+           : make_idesc_f16(BF16, kPT, kPT);
+  constexpr uint32_t kIdesc2 = make_idesc_f16(BF16, PAIR ? 2 * kPT : kPT,
+                                              2 * kPT);
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -206,7 +285,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
   auto sB_hi = [&](int s) {
     return ring + s * C::kStageBytes + (RESA ? 0 : 2 * kPTile);
   };
-  auto sB_lo = [&](int s) { return sB_hi(s) + kPBHalf; };
+  auto sB_lo = [&](int s) { return sB_hi(s) + C::kBHalf; };
   auto sA_hi = [&](int s, int kb) {
     return RESA ? aregion + kb * 2 * kPTile : ring + s * C::kStageBytes;
   };
@@ -221,7 +300,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kPEpiWarps);
+      // PAIR: the even CTA's barrier counts both CTAs' epilogue warps
+      mbar_init(&tempty[a], PAIR ? 2 * kPEpiWarps : kPEpiWarps);
     }
     mbar_init(afull, 1);
     mbar_init(aempty, 1);
@@ -230,26 +310,49 @@ __global__ void __launch_bounds__(kPThreads, 1)
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, 512);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(tmem_holder, 512);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_holder, 512);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // both CTAs' barriers exist before the pair signals across them
+  if constexpr (PAIR) cluster_sync();
   const uint32_t tmem_base = *tmem_holder;
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
+  // PAIR: work items go to clusters; each CTA of a pair takes one tile
+  const int64_t wid = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+  const int64_t wstride =
+      PAIR ? (int64_t)(gridDim.x >> 1) : (int64_t)gridDim.x;
   WaitCtx w{abort_flag, p.status, p.wait_ns};
   const int64_t n = p.n;
 
   // items run chunk-major, and inside a chunk the tiles of the triangle go
   // column by column: CTAs working at the same time share the permuted
   // column panels of the same permutations in L2
-  const int64_t tiles = p.m * (p.m + 1) / 2;
+  const int64_t tiles = PAIR ? col_pairs_before(p.m) : p.m * (p.m + 1) / 2;
+  // PAIR: `dummy` marks the missing partner of a column's last, lone tile:
+  // it repeats its partner's tile and its counts are dropped
+  bool dummy = false;
   auto item_coords = [&](int64_t it, int64_t* row0, int64_t* col0, int* k0,
                          int* klen) {
     const int c = (int)(it / tiles);
     const int64_t t = it % tiles;
     int64_t yt, xt;
-    col_tri_coords(t, &yt, &xt);
+    if constexpr (PAIR) {
+      int64_t r;
+      col_pair_coords(t, &r, &xt);
+      yt = 2 * r + (int64_t)crank;
+      dummy = yt > xt;
+      if (dummy) yt = 2 * r;
+    } else {
+      col_tri_coords(t, &yt, &xt);
+    }
     *row0 = yt * kPT;
     *col0 = xt * kPT;
     *k0 = c * p.chunk;
@@ -269,21 +372,34 @@ __global__ void __launch_bounds__(kPThreads, 1)
       bool a_issued = false;
       uint32_t a_last = 0;
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+      for (int64_t it = wid; it < p.items && ok; it += wstride) {
         int64_t row0, col0;
         int k0, klen;
         item_coords(it, &row0, &col0, &k0, &klen);
         if (klen <= 0) continue;
         if (RESA) {
           if (!mbar_wait(aempty, aph ^ 1u, w)) break;
-          mbar_arrive_expect_tx(afull, (uint32_t)(p.nkb * 2 * kPTile));
           a_issued = true;
           a_last = aph;
-          for (int kb = 0; kb < p.nkb; ++kb) {
-            tma_load_2d_hint(sA_hi(0, kb), &tz_hi, afull, kb * kPK,
-                             (int)row0, pol);
-            tma_load_2d_hint(sA_lo(0, kb), &tz_lo, afull, kb * kPK,
-                             (int)row0, pol);
+          if constexpr (PAIR) {
+            // both CTAs' A tiles count on the even CTA's barrier
+            if (crank == 0)
+              mbar_arrive_expect_tx(afull, (uint32_t)(2 * p.nkb * 2 * kPTile));
+            const uint32_t ab = cluster_addr(afull, 0);
+            for (int kb = 0; kb < p.nkb; ++kb) {
+              tma_load_2d_pair(sA_hi(0, kb), &tz_hi, ab, kb * kPK, (int)row0,
+                               pol);
+              tma_load_2d_pair(sA_lo(0, kb), &tz_lo, ab, kb * kPK, (int)row0,
+                               pol);
+            }
+          } else {
+            mbar_arrive_expect_tx(afull, (uint32_t)(p.nkb * 2 * kPTile));
+            for (int kb = 0; kb < p.nkb; ++kb) {
+              tma_load_2d_hint(sA_hi(0, kb), &tz_hi, afull, kb * kPK,
+                               (int)row0, pol);
+              tma_load_2d_hint(sA_lo(0, kb), &tz_lo, afull, kb * kPK,
+                               (int)row0, pol);
+            }
           }
           aph ^= 1u;
         }
@@ -298,8 +414,41 @@ __global__ void __launch_bounds__(kPThreads, 1)
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&full[stage], bytes);
             const int kc = kb * kPK;
+            if constexpr (PAIR) {
+              // each CTA: (its streamed A and) the 128 B rows of one
+              // permutation, the even CTA k, the odd CTA k + 1 (r_obs and a
+              // lone permutation: the same rows in both); both CTAs' bytes
+              // count on the even CTA's barrier
+              const uint32_t per_cta = (RESA ? 0u : 2u * kPTile) + 2u * kPTile;
+              if (crank == 0)
+                mbar_arrive_expect_tx(&full[stage], 2u * per_cta);
+              const uint32_t fb = cluster_addr(&full[stage], 0);
+              if (!RESA) {
+                tma_load_2d_pair(sA_hi(stage, kb), &tz_hi, fb, kc, (int)row0,
+                                 pol);
+                tma_load_2d_pair(sA_lo(stage, kb), &tz_lo, fb, kc, (int)row0,
+                                 pol);
+              }
+              if (pass < 0) {
+                tma_load_2d_pair(sB_hi(stage), &tz_hi, fb, kc, (int)col0,
+                                 pol);
+                tma_load_2d_pair(sB_lo(stage), &tz_lo, fb, kc, (int)col0,
+                                 pol);
+              } else {
+                const int kk = k0 + 2 * pass + ((two && crank) ? 1 : 0);
+                tma_load_3d_pair(sB_hi(stage), &tp_hi, fb, kc, (int)col0, kk);
+                tma_load_3d_pair(sB_lo(stage), &tp_lo, fb, kc, (int)col0, kk);
+              }
+              issued_mask |= 1u << stage;
+              last_phase[stage] = phase;
+              if (++stage == S) {
+                stage = 0;
+                phase ^= 1u;
+              }
+              continue;
+            }
+            mbar_arrive_expect_tx(&full[stage], bytes);
             if (!RESA) {
               tma_load_2d_hint(sA_hi(stage, kb), &tz_hi, &full[stage], kc,
                                (int)row0, pol);
@@ -333,23 +482,27 @@ __global__ void __launch_bounds__(kPThreads, 1)
           }
         }
       }
+      // drain (PAIR: the even CTA's barriers count both CTAs' copies)
       WaitCtx wd = w;
       volatile int never = 0;
       wd.abort_flag = &never;
-      for (int s = 0; s < S; ++s)
-        if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
-      if (RESA && a_issued) mbar_wait(afull, a_last, wd);
+      if (!PAIR || crank == 0) {
+        for (int s = 0; s < S; ++s)
+          if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
+        if (RESA && a_issued) mbar_wait(afull, a_last, wd);
+      }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && (!PAIR || crank == 0)) {
       // ------------------------------------------------------ MMA issuer
+      // (PAIR: the even CTA issues for both)
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
       uint32_t aphase = 0;
       uint32_t aph = 0;
       bool ok = true;
-      for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+      for (int64_t it = wid; it < p.items && ok; it += wstride) {
         int64_t row0, col0;
         int k0, klen;
         item_coords(it, &row0, &col0, &k0, &klen);
@@ -385,26 +538,46 @@ __global__ void __launch_bounds__(kPThreads, 1)
               const uint64_t dBH = kmajor_desc<64>(bH + off);
               const uint64_t dAL = kmajor_desc<64>(aL + off);
               const uint64_t dBL = kmajor_desc<64>(bL + off);
-              umma_f16(d_tmem, dAH, dBH, idesc, (kb | ks) != 0);
-              umma_f16(d_tmem, dAH, dBL, idesc, 1u);
-              umma_f16(d_tmem, dAL, dBH, idesc, 1u);
-              if (p.lolo) umma_f16(d_tmem, dAL, dBL, idesc, 1u);
+              auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
+                if constexpr (PAIR)
+                  umma_f16_pair(d_tmem, a, b, idesc, acc_in);
+                else
+                  umma_f16(d_tmem, a, b, idesc, acc_in);
+              };
+              mma(dAH, dBH, (kb | ks) != 0);
+              mma(dAH, dBL, 1u);
+              mma(dAL, dBH, 1u);
+              if (p.lolo) mma(dAL, dBL, 1u);
             }
-            umma_commit(&empty[stage]);
+            if constexpr (PAIR)
+              umma_commit_pair(&empty[stage], 3);  // frees it in both CTAs
+            else
+              umma_commit(&empty[stage]);
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
             }
           }
           if (!ok) break;
-          umma_commit(&tfull[acc]);
+          if constexpr (PAIR)
+            umma_commit_pair(&tfull[acc], 3);  // each CTA reads its rows
+          else
+            umma_commit(&tfull[acc]);
           acc ^= 1;
           if (acc == 0) aphase ^= 1u;
         }
         // the resident A tile is free once this item's MMAs complete
-        if (RESA && ok) umma_commit(aempty);
+        if (RESA && ok) {
+          if constexpr (PAIR)
+            umma_commit_pair(aempty, 3);
+          else
+            umma_commit(aempty);
+        }
       }
-      umma_commit(mdone);
+      if constexpr (PAIR)
+        umma_commit_pair(mdone, 1);
+      else
+        umma_commit(mdone);
       WaitCtx wd = w;
       volatile int never = 0;
       wd.abort_flag = &never;
@@ -417,7 +590,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     int acc = 0;
     uint32_t aphase = 0;
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < p.items && ok; it += gridDim.x) {
+    for (int64_t it = wid; it < p.items && ok; it += wstride) {
       int64_t row0, col0;
       int k0, klen;
       item_coords(it, &row0, &col0, &k0, &klen);
@@ -463,14 +636,19 @@ __global__ void __launch_bounds__(kPThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[acc]);
+        if (lane == 0) {
+          if (PAIR && crank != 0)  // released to the even CTA's MMA issuer
+            mbar_arrive_cluster(cluster_addr(&tempty[acc], 0));
+          else
+            mbar_arrive(&tempty[acc]);
+        }
         acc ^= 1;
         if (acc == 0) aphase ^= 1u;
       }
       if (!ok) break;
       // add this item's counts to the packed output
       const int64_t i = row0 + q * 32 + lane;
-      if (i < n && p.flags[i] == 0) {
+      if (!dummy && i < n && p.flags[i] == 0) {
         const int64_t base = pair_row_base(n, i);
 #pragma unroll
         for (int t = 0; t < 64; ++t) {
@@ -486,20 +664,64 @@ __global__ void __launch_bounds__(kPThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if constexpr (PAIR) {
+    // after an abort, the odd CTA's last copies are counted on barriers no
+    // one waits for any more: give them time to land (bounded, error path)
+    if (*abort_flag && threadIdx.x == 0) {
+      const uint64_t t0 = global_timer_ns();
+      while (global_timer_ns() - t0 < 200000u) {
+      }
+    }
+    __syncthreads();
+    // neither CTA leaves while the other may still use its memory or TMEM
+    cluster_sync();
+  }
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem_base, 512);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem_base, 512);
+    else
+      tmem_dealloc(tmem_base, 512);
   }
 }
 
-template <bool BF16, bool RESA>
+template <bool BF16, bool RESA, bool PAIR>
 cudaError_t launch_perm_kernel(const pcc_zmat* Z, const CUtensorMap& ph,
                                const CUtensorMap& pl, const PermParams& p,
                                cudaStream_t s) {
-  auto fn = k_perm_tc<BF16, RESA>;
-  const int smem = PCfg<RESA>::kSmemBytes;
+  auto fn = k_perm_tc<BF16, RESA, PAIR>;
+  const int smem = PCfg<RESA, PAIR>::kSmemBytes;
   cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
+  if constexpr (PAIR) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kPThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters = 0;  // per template instance
+    if (max_clusters == 0) {
+      cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
+      int mc = 0;
+      if (cudaOccupancyMaxActiveClusters(&mc, fn, &cfg) != cudaSuccess ||
+          mc <= 0) {
+        cudaGetLastError();
+        mc = num_sms(Z->device) / 2;
+      }
+      max_clusters = mc;
+    }
+    const int64_t ncl = p.items < max_clusters ? p.items : max_clusters;
+    cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, fn, Z->tm_hi32, Z->tm_lo32, ph, pl, p);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   int64_t grid = num_sms(Z->device);
   if (p.items < grid) grid = p.items;
   fn<<<(unsigned)grid, kPThreads, smem, s>>>(Z->tm_hi32, Z->tm_lo32, ph, pl,
@@ -547,7 +769,9 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
   uint16_t* wh = static_cast<uint16_t*>(Z->perm_ws);
   const bool bf16 = Z->prec != PCC_PREC_FP16X3S;
   const int64_t m = (n + kPT - 1) / kPT;
-  const int64_t tiles = m * (m + 1) / 2;
+  // the CTA-pair form takes the tiles of a column two at a time
+  const bool pair = tc_tuning().pair_mma != 0 && m >= 2;
+  const int64_t tiles = pair ? col_pairs_before(m) : m * (m + 1) / 2;
   const int sms = num_sms(Z->device);
   if ((size_t)lpad * 4 + (size_t)kGatherWarps * 4 * lpad > 200 * 1024)
     return PCC_ERR_UNSUPPORTED;  // rows longer than the gather stages
@@ -559,17 +783,9 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     const int64_t rpb = 64;
     dim3 g((unsigned)((n + rpb - 1) / rpb), (unsigned)kbatch, 1);
     const size_t gsmem = (size_t)lpad * 4 + (size_t)kGatherWarps * 4 * lpad;
-    if (gsmem > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_perm_gather,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)gsmem);
-      if (e != cudaSuccess) return cuda_status(e);
-    }
-    k_perm_gather<<<g, kGatherWarps * 32, gsmem, s>>>(
-        static_cast<const uint16_t*>(Z->hi),
-        static_cast<const uint16_t*>(Z->lo), d_perms, n, Z->l, lpad, kb0, rpb,
-        wh, wl, Z->status);
-    e = cudaGetLastError();
+    e = launch_gather(g, gsmem, s, static_cast<const uint16_t*>(Z->hi),
+                      static_cast<const uint16_t*>(Z->lo), d_perms, n, Z->l,
+                      lpad, kb0, rpb, wh, wl, Z->status);
     if (e != cudaSuccess) return cuda_status(e);
     CUtensorMap ph, pl;
     if (!encode_tmap_3d_u16(&ph, wh, kbatch, n, lpad, kPT, kPK, bf16) ||
@@ -578,9 +794,10 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     // chunks of about kPermChunk permutations: short enough that the
     // permuted panels in flight fit in L2, long enough that r_obs (one
     // extra pass per item) stays a few percent; and at least ~8 items per SM
+    const int64_t workers = pair ? sms / 2 : sms;  // CTAs or CTA pairs
     int64_t chunk = kPermChunk;
-    if (tiles * ((kbatch + chunk - 1) / chunk) < 8 * (int64_t)sms)
-      chunk = (kbatch * tiles + 8 * (int64_t)sms - 1) / (8 * (int64_t)sms);
+    if (tiles * ((kbatch + chunk - 1) / chunk) < 8 * workers)
+      chunk = (kbatch * tiles + 8 * workers - 1) / (8 * workers);
     if (chunk < 1) chunk = 1;
     if (chunk > kbatch) chunk = kbatch;
     const int64_t nchunks = (kbatch + chunk - 1) / chunk;
@@ -597,12 +814,21 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     p.counts = d_counts;
     p.status = Z->status;
     p.wait_ns = wait_limit_ns();
-    if (lpad <= kPMaxResidentK)
-      e = bf16 ? launch_perm_kernel<true, true>(Z, ph, pl, p, s)
-               : launch_perm_kernel<false, true>(Z, ph, pl, p, s);
-    else
-      e = bf16 ? launch_perm_kernel<true, false>(Z, ph, pl, p, s)
-               : launch_perm_kernel<false, false>(Z, ph, pl, p, s);
+    if (pair) {
+      if (lpad <= kPMaxResidentK)
+        e = bf16 ? launch_perm_kernel<true, true, true>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, true, true>(Z, ph, pl, p, s);
+      else
+        e = bf16 ? launch_perm_kernel<true, false, true>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, false, true>(Z, ph, pl, p, s);
+    } else {
+      if (lpad <= kPMaxResidentK)
+        e = bf16 ? launch_perm_kernel<true, true, false>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, true, false>(Z, ph, pl, p, s);
+      else
+        e = bf16 ? launch_perm_kernel<true, false, false>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, false, false>(Z, ph, pl, p, s);
+    }
     if (e != cudaSuccess) return cuda_status(e);
   }
   return PCC_OK;

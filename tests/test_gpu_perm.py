@@ -163,3 +163,49 @@ def test_perm_full_config_sampled(pcc_gpu):
     J = np.concatenate([J, m0[mj]])
     exact, tot = check_band(X, perms, got, I, J)
     assert exact > 0.5 * tot
+
+
+@pytest.mark.parametrize("n,l,P,prec", [
+    (300, 33, 41, "fp16x3s"),    # 3 tile columns: lone diagonal tiles
+    (520, 200, 40, "bf16x3"),    # 5 tile columns, resident A
+    (400, 300, 17, "bf16x4"),    # rows longer than 256: streamed A
+    (129, 64, 7, "fp16x3s"),     # two tile columns, odd P
+])
+def test_perm_pair_mma_equals_single_cta(pcc_gpu, n, l, P, prec):
+    """The CTA-pair form (one 2-SM MMA for two tiles of a tile column, one
+    permutation's column rows loaded by each CTA) gives the single-CTA
+    form's counts exactly, including the lone last tile of a column, an odd
+    number of permutations and a resumed range."""
+    pcc = pcc_gpu
+    X = synth.counts_log(n, l, seed=n + 5 * l)
+    X[n // 3] = 1.5
+    perms = synth.fisher_yates_perms(P, l, seed=P)
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(pair_mma=0)
+        ref, st0, Z = gpu_perm_counts(pcc, X, perms, prec)
+        pcc.pcc_set_tuning(pair_mma=1)
+        got, st1, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z)
+        part, st2, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z,
+                                       ranges=[(0, 5), (5, P)])
+    finally:
+        pcc.pcc_set_tuning(pair_mma=before["pair_mma"])
+    assert st0 == st1 == st2 == 0
+    assert ref.max() > 0
+    assert np.array_equal(got, ref)
+    assert np.array_equal(part, ref)
+
+
+@pytest.mark.parametrize("l", [700, 1100])
+def test_perm_counts_long_rows(pcc_gpu, l):
+    """Rows of 512-1024 samples (the gather keeps four groups of indices
+    per lane in registers) and longer (indices read from shared memory),
+    both with the streamed A operand."""
+    n = 140
+    X = synth.counts_log(n, l, seed=l)
+    perms = synth.fisher_yates_perms(6, l, seed=l + 1)
+    got, st, _ = gpu_perm_counts(pcc_gpu, X, perms, "bf16x3")
+    assert st == 0
+    I, J = np.triu_indices(n, 1)
+    exact, total = check_band(X, perms, got, I, J)
+    assert exact > 0.5 * total
