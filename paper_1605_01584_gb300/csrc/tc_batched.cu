@@ -12,8 +12,12 @@
 // per matrix at run time, so one kernel serves the whole batch.
 //
 // Same roles, pipeline and bounded waits as the single-matrix kernel
-// (tc_pairs.cu), single CTAs, K = 32 per stage; matrices with rows longer
-// than 1024 split their K blocks over two accumulators as that kernel does.
+// (tc_pairs.cu), K = 32 per stage; matrices with rows longer than 1024 split
+// their K blocks over two accumulators as that kernel does.  With the pair
+// form (pcc_set_pair_mma, the default) the plan hands whole super-tiles to
+// CTA pairs, which run one 2-SM MMA per tile (M = 256, each CTA loading its
+// 128 A rows and 128 of the B rows, as in tc_pairs.cu); otherwise single
+// CTAs take units.
 #include <math.h>
 
 #include <algorithm>
@@ -33,12 +37,17 @@ namespace {
 constexpr int kBM = 128, kBN = 256, kKB = 32, kUK = 16;
 constexpr int kThreads = 320, kEpiWarps = 8;
 constexpr int kTileA = kBM * kKB * 2;            // 8 KB
-constexpr int kTileB = kBN * kKB * 2;            // 16 KB
-constexpr int kStageBytes = 2 * (kTileA + kTileB);  // 48 KB (3 products)
-constexpr int kStages = 4;
 constexpr int kEpiBytes = kEpiWarps * 32 * kStagePad * 4;
-constexpr int kSmemBytes = 1024 + kStages * kStageBytes + kEpiBytes + 256;
-static_assert(kSmemBytes <= 232448, "shared memory budget");
+// PAIR: each CTA holds 128 of the 256 B rows, so six smaller stages
+template <bool PAIR>
+struct BCfg {
+  static constexpr int kTileB = (PAIR ? kBM : kBN) * kKB * 2;
+  static constexpr int kStageBytes = 2 * (kTileA + kTileB);  // 3 products
+  static constexpr int kStages = PAIR ? 6 : 4;
+  static constexpr int kSmemBytes =
+      1024 + kStages * kStageBytes + kEpiBytes + 256;
+  static_assert(kSmemBytes <= 232448, "shared memory budget");
+};
 
 struct alignas(64) MatDesc {
   CUtensorMap tm_hi;  // box 32 x 128, 64-B swizzle
@@ -56,8 +65,9 @@ struct alignas(64) MatDesc {
 
 struct BatchParams {
   const MatDesc* descs;
-  const uint64_t* items;   // (matrix << 40) | unit
-  const int64_t* cta_off;  // items of CTA c: [cta_off[c], cta_off[c+1])
+  const uint64_t* items;   // (matrix << 40) | unit (PAIR: | tile)
+  const int64_t* cta_off;  // items of CTA (PAIR: CTA pair) c:
+                           // [cta_off[c], cta_off[c+1])
   int64_t G;               // band height
   int* status;
   uint64_t wait_ns;
@@ -66,8 +76,13 @@ struct BatchParams {
 constexpr int kItemShift = 40;
 constexpr uint64_t kItemMask = (1ull << kItemShift) - 1;
 
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_tc_batched(const BatchParams p) {
+  using C = BCfg<PAIR>;
+  constexpr int kTileB = C::kTileB;
+  constexpr int kStageBytes = C::kStageBytes;
+  constexpr int kStages = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -98,22 +113,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kEpiWarps);
+      // PAIR: the even CTA's barrier counts both CTAs' epilogue warps
+      mbar_init(&tempty[a], PAIR ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(mdone, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_holder, 512);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(tmem_holder, 512);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(tmem_holder, 512);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // both CTAs' barriers exist before the pair signals across them
+  if constexpr (PAIR) cluster_sync();
   const uint32_t tmem_base = *tmem_holder;
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
   WaitCtx w{abort_flag, p.status, p.wait_ns};
-  const int64_t it0 = p.cta_off[blockIdx.x], it1 = p.cta_off[blockIdx.x + 1];
+  const int64_t wid = PAIR ? (int64_t)(blockIdx.x >> 1) : (int64_t)blockIdx.x;
+  const int64_t it0 = p.cta_off[wid], it1 = p.cta_off[wid + 1];
 
   // unit coordinates; the band cursor restarts when the matrix changes
   struct Walk {
@@ -129,9 +154,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       wk.b = b;
       band_cursor_init(&wk.cur, d->m, p.G);
     }
+    // PAIR items are tiles, CTA rank h takes half h; else items are units
+    const int64_t t = PAIR ? u : (u >> 1);
+    const int64_t half = PAIR ? (int64_t)crank : (u & 1);
     int64_t yt, xt;
-    band_tile_coords(&wk.cur, d->m, p.G, u >> 1, &yt, &xt);
-    *row0 = yt * kTcSuper + (u & 1) * kBM;
+    band_tile_coords(&wk.cur, d->m, p.G, t, &yt, &xt);
+    *row0 = yt * kTcSuper + half * kBM;
     *col0 = xt * kTcSuper;
   };
 
@@ -155,8 +183,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[stage], bytes);
           const int kc = kb * kKB;
+          if constexpr (PAIR) {
+            // each CTA: its 128 A rows and 128 of the B rows; both CTAs'
+            // bytes count on the even CTA's barrier
+            if (crank == 0) mbar_arrive_expect_tx(&full[stage], 2 * bytes);
+            const uint32_t fb = cluster_addr(&full[stage], 0);
+            const int brow = (int)(col0 + crank * kBM);
+            tma_load_2d_pair(sA_hi(stage), &d->tm_hi, fb, kc, (int)row0, pol);
+            tma_load_2d_pair(sB_hi(stage), &d->tm_hi, fb, kc, brow, pol);
+            if (nprod >= 3) {
+              tma_load_2d_pair(sA_lo(stage), &d->tm_lo, fb, kc, (int)row0,
+                               pol);
+              tma_load_2d_pair(sB_lo(stage), &d->tm_lo, fb, kc, brow, pol);
+            }
+            issued_mask |= 1u << stage;
+            last_phase[stage] = phase;
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
+            }
+            continue;
+          }
+          mbar_arrive_expect_tx(&full[stage], bytes);
           tma_load_2d_hint(sA_hi(stage), &d->tm_hi, &full[stage], kc,
                            (int)row0, pol);
           tma_load_2d_hint(sB_hi(stage), &d->tm_hi, &full[stage], kc,
@@ -179,14 +228,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      // drain (PAIR: the even CTA's barriers count both CTAs' copies)
       WaitCtx wd = w;
       volatile int never = 0;
       wd.abort_flag = &never;
-      for (int s = 0; s < kStages; ++s)
-        if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
+      if (!PAIR || crank == 0)
+        for (int s = 0; s < kStages; ++s)
+          if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
     }
   } else if (warp == 1) {
-    if (lane == 0) {
+    // MMA issuer (PAIR: the even CTA issues for both)
+    if (lane == 0 && (!PAIR || crank == 0)) {
       Walk wk;
       int stage = 0, acc = 0;
       uint32_t phase = 0, aphase = 0;
@@ -224,28 +276,44 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t off = ks * kUK * 2;
             const uint64_t dAH = kmajor_desc<64>(aH + off);
             const uint64_t dBH = kmajor_desc<64>(bH + off);
-            umma_f16(d_tmem, dAH, dBH, idesc, (first && ks == 0) ? 0u : 1u);
+            auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
+              if constexpr (PAIR)
+                umma_f16_pair(d_tmem, a, b, idesc, acc_in);
+              else
+                umma_f16(d_tmem, a, b, idesc, acc_in);
+            };
+            mma(dAH, dBH, (first && ks == 0) ? 0u : 1u);
             if (nprod >= 3) {
-              umma_f16(d_tmem, dAH, kmajor_desc<64>(bL + off), idesc, 1u);
-              umma_f16(d_tmem, kmajor_desc<64>(aL + off), dBH, idesc, 1u);
+              mma(dAH, kmajor_desc<64>(bL + off), 1u);
+              mma(kmajor_desc<64>(aL + off), dBH, 1u);
               if (nprod == 4)
-                umma_f16(d_tmem, kmajor_desc<64>(aL + off),
-                         kmajor_desc<64>(bL + off), idesc, 1u);
+                mma(kmajor_desc<64>(aL + off), kmajor_desc<64>(bL + off), 1u);
             }
           }
-          umma_commit(&empty[stage]);
+          if constexpr (PAIR)
+            umma_commit_pair(&empty[stage], 3);  // frees it in both CTAs
+          else
+            umma_commit(&empty[stage]);
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
         }
         if (!ok) break;
-        umma_commit(&tfull[acc0]);
-        if (kalt) umma_commit(&tfull[acc]);
+        if constexpr (PAIR) {
+          umma_commit_pair(&tfull[acc0], 3);
+          if (kalt) umma_commit_pair(&tfull[acc], 3);
+        } else {
+          umma_commit(&tfull[acc0]);
+          if (kalt) umma_commit(&tfull[acc]);
+        }
         acc ^= 1;
         if (acc == 0) aphase ^= 1u;
       }
-      umma_commit(mdone);
+      if constexpr (PAIR)
+        umma_commit_pair(mdone, 1);
+      else
+        umma_commit(mdone);
       WaitCtx wd = w;
       volatile int never = 0;
       wd.abort_flag = &never;
@@ -300,8 +368,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
-        mbar_arrive(&tempty[acc0]);
-        if (kalt) mbar_arrive(&tempty[acc]);
+        if (PAIR && crank != 0) {  // released to the even CTA's MMA issuer
+          mbar_arrive_cluster(cluster_addr(&tempty[acc0], 0));
+          if (kalt) mbar_arrive_cluster(cluster_addr(&tempty[acc], 0));
+        } else {
+          mbar_arrive(&tempty[acc0]);
+          if (kalt) mbar_arrive(&tempty[acc]);
+        }
       }
       acc ^= 1;
       if (acc == 0) aphase ^= 1u;
@@ -311,9 +384,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if constexpr (PAIR) {
+    // after an abort, the odd CTA's last copies are counted on barriers no
+    // one waits for any more: give them time to land (bounded, error path)
+    if (*abort_flag && threadIdx.x == 0) {
+      const uint64_t t0 = global_timer_ns();
+      while (global_timer_ns() - t0 < 200000u) {
+      }
+    }
+    __syncthreads();
+    // neither CTA leaves while the other may still use its memory or TMEM
+    cluster_sync();
+  }
   if (warp == 1) {
     __syncwarp();
-    tmem_dealloc(tmem_base, 512);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem_base, 512);
+    else
+      tmem_dealloc(tmem_base, 512);
   }
 }
 
@@ -323,8 +411,9 @@ struct Plan {
   std::vector<float*> rs;
   std::vector<int64_t> sig;  // n, lpad, prec, hi address per matrix
   TcTuning tuning;
+  bool pair = false;  // items are tiles for CTA pairs (2-SM MMA)
   int device = -1;
-  int grid = 0;
+  int grid = 0;       // CTAs
   void* dmem = nullptr;  // descs | cta_off | items
   MatDesc* d_descs = nullptr;
   int64_t* d_off = nullptr;
@@ -334,10 +423,39 @@ struct Plan {
 std::mutex g_plan_mu;
 std::vector<Plan*> g_plans;  // small cache, most recent last
 
+// CTA pairs of the pair form that can be resident at once
+int pair_workers(int device) {
+  static int mc = 0;
+  if (mc == 0) {
+    auto fn = k_pairs_tc_batched<true>;
+    const int smem = BCfg<true>::kSmemBytes;
+    int v = 0;
+    if (ensure_func_smem(reinterpret_cast<const void*>(fn), smem) ==
+        cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.blockDim = dim3(kThreads, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cfg.gridDim = dim3(2 * (unsigned)(num_sms(device) / 2), 1, 1);
+      if (cudaOccupancyMaxActiveClusters(&v, fn, &cfg) != cudaSuccess) v = 0;
+    }
+    cudaGetLastError();
+    mc = v > 0 ? v : num_sms(device) / 2;
+  }
+  return mc;
+}
+
 bool build_plan(Plan* P) {
   const int B = (int)P->zs.size();
   const int sms = num_sms(P->device);
   const TcTuning tn = tc_tuning();
+  const bool pair = P->pair;
   std::vector<MatDesc> descs(B);
   struct U {
     double cost;
@@ -357,12 +475,22 @@ bool build_plan(Plan* P) {
               : Z->prec == PCC_PREC_BF16X4 ? 4
                                            : 3;
     d.kalt = (Z->lpad > tc_tuning().kalt_min_l && d.nkb >= 2) ? 1 : 0;
-    d.idesc = make_idesc_f16(Z->prec != PCC_PREC_FP16X3S, kBM, kBN);
+    // the pair form's one instruction covers both CTAs' 128 rows
+    d.idesc =
+        make_idesc_f16(Z->prec != PCC_PREC_FP16X3S, pair ? 2 * kBM : kBM, kBN);
     d.scale = (float)ldexp(1.0, -2 * Z->scale_exp);
     d.flags = Z->flags;
     d.R = P->rs[b];
-    const int64_t nu = 2 * tc_num_tiles(Z->n);
+    // a unit's cost; a tile of the pair form costs the same (its two
+    // halves run side by side on the pair)
     const double cost = tn.cost_c0 + tn.cost_c1 * d.nkb * d.nprod;
+    if (pair) {
+      const int64_t nt = tc_num_tiles(Z->n);
+      for (int64_t t = 0; t < nt; ++t)
+        units.push_back({cost, ((uint64_t)b << kItemShift) | (uint64_t)t});
+      continue;
+    }
+    const int64_t nu = 2 * tc_num_tiles(Z->n);
     BandCursor cur;
     band_cursor_init(&cur, d.m, tc_tuning().band);
     for (int64_t u = 0; u < nu; ++u) {
@@ -373,7 +501,9 @@ bool build_plan(Plan* P) {
     }
   }
   const int64_t total = (int64_t)units.size();
-  int grid = (int)std::min<int64_t>(sms, std::max<int64_t>(total, 1));
+  // workers: CTAs, or CTA pairs in the pair form
+  const int64_t nw = pair ? pair_workers(P->device) : sms;
+  int grid = (int)std::min<int64_t>(nw, std::max<int64_t>(total, 1));
   // longest first, each to the least-loaded CTA
   std::stable_sort(units.begin(), units.end(),
                    [](const U& a, const U& b) { return a.cost > b.cost; });
@@ -421,7 +551,7 @@ bool build_plan(Plan* P) {
     P->dmem = nullptr;
     return false;
   }
-  P->grid = grid;
+  P->grid = pair ? 2 * grid : grid;
   return true;
 }
 
@@ -437,7 +567,8 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
       if ((int)q->zs.size() != B || q->device != dev) continue;
       bool same = q->tuning.band == tc_tuning().band &&
                   q->tuning.cost_c0 == tc_tuning().cost_c0 &&
-                  q->tuning.cost_c1 == tc_tuning().cost_c1;
+                  q->tuning.cost_c1 == tc_tuning().cost_c1 &&
+                  q->pair == (tc_tuning().pair_mma != 0);
       for (int b = 0; b < B && same; ++b)
         same = q->zs[b] == Zs[b] && q->rs[b] == Rs[b] &&
                q->sig[4 * b] == Zs[b]->n && q->sig[4 * b + 1] == Zs[b]->lpad &&
@@ -459,6 +590,7 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
         P->sig.push_back((int64_t)(uintptr_t)Zs[b]->hi);
       }
       P->tuning = tc_tuning();
+      P->pair = tc_tuning().pair_mma != 0;
       P->device = dev;
       if (!build_plan(P)) {
         delete P;
@@ -474,9 +606,6 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
       }
     }
   }
-  cudaError_t e = ensure_func_smem(
-      reinterpret_cast<const void*>(k_pairs_tc_batched), kSmemBytes);
-  if (e != cudaSuccess) return cuda_status(e);
   BatchParams bp;
   bp.descs = P->d_descs;
   bp.items = P->d_items;
@@ -484,7 +613,32 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
   bp.G = tc_tuning().band;
   bp.status = Zs[0]->status;
   bp.wait_ns = wait_limit_ns();
-  k_pairs_tc_batched<<<P->grid, kThreads, kSmemBytes, s>>>(bp);
+  if (P->pair) {
+    auto fn = k_pairs_tc_batched<true>;
+    const int smem = BCfg<true>::kSmemBytes;
+    cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)P->grid, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, fn, bp);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaGetLastError());
+  }
+  auto fn = k_pairs_tc_batched<false>;
+  const int smem = BCfg<false>::kSmemBytes;
+  cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return cuda_status(e);
+  fn<<<P->grid, kThreads, smem, s>>>(bp);
   return cuda_status(cudaGetLastError());
 }
 

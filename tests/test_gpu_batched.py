@@ -123,3 +123,31 @@ def test_batched_invalid_arguments(pcc_gpu):
         pcc.pcc_allpairs_upper_batched([Z32], [R])
     with pytest.raises(pcc.PccError):
         pcc.pcc_allpairs_upper_batched([], [])
+
+
+def test_batched_pair_mma_equals_single_ctas(pcc_gpu):
+    """The pair form (whole tiles to CTA pairs, one 2-SM MMA each) and the
+    single-CTA form (units to CTAs) give the same bits; switching the form
+    builds a new plan."""
+    torch = _torch()
+    pcc = pcc_gpu
+    Xs, Zs, Rs = _setup(pcc, SHAPES, seed0=950)
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(pair_mma=0)
+        pcc.pcc_allpairs_upper_batched(Zs, Rs)
+        ref = [r.cpu().numpy().copy() for r in Rs]
+        for r in Rs:
+            r.fill_(7.0)
+        pcc.pcc_set_tuning(pair_mma=1)
+        pcc.pcc_allpairs_upper_batched(Zs, Rs)
+        assert pcc.pcc_sync_status(Zs[0]) == 0
+    finally:
+        pcc.pcc_set_tuning(pair_mma=before["pair_mma"])
+    for b in range(len(SHAPES)):
+        got = Rs[b].cpu().numpy()
+        assert not np.any(got == 7.0), b
+        assert np.array_equal(np.isnan(got), np.isnan(ref[b]))
+        ok = ~np.isnan(got)
+        assert np.array_equal(got[ok].view(np.uint32),
+                              ref[b][ok].view(np.uint32)), b
