@@ -168,6 +168,42 @@ def test_standardize_forms(pcc_gpu):
             Z.close()
 
 
+@pytest.mark.parametrize("l", [7, 100, 128, 200, 256, 500, 512])
+def test_standardize_row_pitch_gives_same_bits(pcc_gpu, l):
+    """16-byte aligned rows are read with float4 loads, rows with an odd
+    pitch with scalar loads; both sum in the same order, so the stored
+    halves and flags are the same bits (FP16X3S, BF16X3, FP32)."""
+    torch = _torch()
+    n = 333
+    X = _data(n, l, seed=40 + l)
+    wide = np.zeros((n, l + 1), dtype=np.float32)
+    wide[:, :l] = X
+    Xa = torch.from_numpy(X).cuda()                 # pitch l (aligned if 4 | l)
+    Xu = torch.from_numpy(wide).cuda()[:, :l]       # pitch l + 1
+    for prec in ("fp16x3s", "bf16x3", "fp32"):
+        za = pcc_gpu.pcc_standardize(Xa, prec)
+        zu = pcc_gpu.pcc_standardize(Xu, prec)
+        lpad = za.info()["lpad"]
+        ba, bu = za.buffers(), zu.buffers()
+        for key in ("hi", "lo", "z"):
+            if not ba[key]:
+                continue
+            bytes_per = 4 if key == "z" else 2
+            a = torch.empty(n * lpad * bytes_per, dtype=torch.uint8,
+                            device="cuda")
+            u = torch.empty_like(a)
+            _copy_from_ptr(a, ba[key])
+            _copy_from_ptr(u, bu[key])
+            assert torch.equal(a, u), (prec, key, l)
+        fa = torch.empty(n, dtype=torch.uint8, device="cuda")
+        fu = torch.empty_like(fa)
+        _copy_from_ptr(fa, ba["flags"])
+        _copy_from_ptr(fu, bu["flags"])
+        assert torch.equal(fa, fu)
+        za.close()
+        zu.close()
+
+
 def _copy_from_ptr(dst, ptr):
     """Device-to-device copy from a raw library-owned pointer (driver API,
     unified addressing)."""
