@@ -500,8 +500,9 @@ def run_batched(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        for Xd, Z in zip(Xs, Zs):
-            pcc.pcc_standardize(Xd, args.prec, Z=Z)
+        # every matrix's standardize in one launch, then every matrix's
+        # pairs in one launch
+        pcc.pcc_standardize_batched(Xs, args.prec, Zs=Zs)
         pcc.pcc_allpairs_upper_batched(Zs, Rs)
 
     ms = _timed(step, max(3, min(args.steps, 10)), args.warmup, stream)

@@ -105,6 +105,27 @@ pcc_status pcc_standardize(const void *X, pcc_dtype xt, int64_t n, int64_t l,
                            int64_t ldx, pcc_prec prec, pcc_zmat **Z,
                            void *stream);
 
+/* pcc_standardize for B FP32 matrices at once (Eq. 5 / Algorithm 3 applied
+ * to each; the batching is this library's, for the many-datasets workload):
+ * one launch per stored form covers up to 96 matrices, each with its own
+ * n, l and pitch, so small matrices do not each pay a launch.  The results
+ * are the same bits as B pcc_standardize calls.
+ *   Xs[b]   device, ns[b] x ls[b] FP32, row-major, leading dimension
+ *           ldxs[b] >= ls[b]; the arrays Xs, ns, ls, ldxs, Zs are host
+ *           arrays of B entries.
+ *   Zs[b]   as pcc_standardize's *Z: reused when it matches (device, n, l,
+ *           precision), otherwise replaced by a new pcc_zmat (an old one is
+ *           left to the caller).  prec applies to every matrix (AUTO is
+ *           resolved per matrix from its l).
+ * Errors: PCC_ERR_INVALID_ARG for B < 1, a NULL array or X, or any matrix
+ * pcc_standardize would reject (checked before anything is allocated or
+ * launched); PCC_ERR_OOM (the Zs created so far are returned);
+ * PCC_ERR_UNSUPPORTED as pcc_standardize. */
+pcc_status pcc_standardize_batched(const float *const *Xs, const int64_t *ns,
+                                   const int64_t *ls, const int64_t *ldxs,
+                                   int32_t B, pcc_prec prec, pcc_zmat **Zs,
+                                   void *stream);
+
 /* Free a pcc_zmat (waits for nothing: the caller must have synchronised
  * the streams that use it).  NULL is accepted. */
 pcc_status pcc_zmat_destroy(pcc_zmat *Z);

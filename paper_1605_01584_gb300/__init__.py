@@ -86,6 +86,8 @@ def load(path: str | None = None):
         "pcc_standardize": (_ST, [_P, _I32, _I64, _I64, _I64, _I32,
                                   ctypes.POINTER(_P), _P]),
         "pcc_zmat_destroy": (_ST, [_P]),
+        "pcc_standardize_batched": (_ST, [_P, _P, _P, _P, _I32, _I32, _P,
+                                          _P]),
         "pcc_zmat_info": (_ST, [_P, _P, _P, _P, _P, _P]),
         "pcc_zmat_buffers": (_ST, [_P, _P, _P, _P, _P]),
         "pcc_num_tiles": (_I64, [_P]),
@@ -207,6 +209,30 @@ def pcc_standardize(X, prec="auto", Z: Zmat | None = None, stream=None,
     if Z is not None and h.value == Z.handle.value:
         return Z
     return Zmat(h.value)
+
+
+def pcc_standardize_batched(Xs, prec="auto", Zs=None, stream=None):
+    """pcc_standardize for many FP32 device matrices in one launch per
+    stored form.  Zs (optional): matching Zmats are reused in place; returns
+    the list of Zmats (new ones where a shape or form changed)."""
+    import torch
+    B = len(Xs)
+    for X in Xs:
+        assert X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+        assert X.dtype == torch.float32
+    xs = (_P * B)(*[X.data_ptr() for X in Xs])
+    ns = (_I64 * B)(*[X.shape[0] for X in Xs])
+    ls = (_I64 * B)(*[X.shape[1] for X in Xs])
+    lds = (_I64 * B)(*[X.stride(0) for X in Xs])
+    old = list(Zs) if Zs is not None else [None] * B
+    hs = (_P * B)(*[z.handle.value if z is not None else None for z in old])
+    _check(load().pcc_standardize_batched(xs, ns, ls, lds, B, _prec(prec),
+                                          hs, _stream(stream)),
+           "pcc_standardize_batched")
+    out = []
+    for z, h in zip(old, hs):
+        out.append(z if z is not None and h == z.handle.value else Zmat(h))
+    return out
 
 
 def pcc_allpairs_upper(Z: Zmat, R, tile_begin: int = 0, tile_end: int = -1,

@@ -291,6 +291,33 @@ pcc_status pcc_standardize(const void* X, pcc_dtype xt, int64_t n, int64_t l,
                                         static_cast<cudaStream_t>(stream)));
 }
 
+pcc_status pcc_standardize_batched(const float* const* Xs, const int64_t* ns,
+                                   const int64_t* ls, const int64_t* ldxs,
+                                   int32_t B, pcc_prec prec, pcc_zmat** Zs,
+                                   void* stream) {
+  if (B < 1 || !Xs || !ns || !ls || !ldxs || !Zs || (int)prec < 0 ||
+      prec > PCC_PREC_AUTO)
+    return PCC_ERR_INVALID_ARG;
+  for (int32_t b = 0; b < B; ++b)
+    if (!Xs[b] || ns[b] < 2 || ls[b] < 2 || ldxs[b] < ls[b] ||
+        ns[b] >= (1ll << 31) || ls[b] >= (1ll << 31))
+      return PCC_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PCC_ERR_CUDA;
+  for (int32_t b = 0; b < B; ++b) {
+    const pcc_prec rp = resolve_prec(prec, ls[b]);
+    if (is_split(rp) && !device_is_sm103(dev)) return PCC_ERR_UNSUPPORTED;
+    if (!zmat_matches(Zs[b], dev, ns[b], ls[b], rp)) {
+      pcc_zmat* nz = nullptr;
+      pcc_status st = zmat_create(dev, ns[b], ls[b], rp, &nz);
+      if (st != PCC_OK) return st;
+      Zs[b] = nz;
+    }
+  }
+  return cuda_status(launch_standardize_batched(
+      Xs, ldxs, Zs, B, static_cast<cudaStream_t>(stream)));
+}
+
 pcc_status pcc_zmat_destroy(pcc_zmat* Z) {
   if (!Z) return PCC_OK;
   int cur = 0;

@@ -78,6 +78,12 @@ void tc_set_tuning(const TcTuning& t);
 // K1: standardize rows of X into Z's storage.
 cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
                                pcc_zmat* Z, cudaStream_t s);
+// K1 for many FP32 matrices: one launch per stored form and up to
+// kStdBatchMax matrices (the matrix table is a kernel parameter).
+constexpr int kStdBatchMax = 96;
+cudaError_t launch_standardize_batched(const float* const* Xs,
+                                       const int64_t* ldxs, pcc_zmat* const* Zs,
+                                       int count, cudaStream_t s);
 
 // K4/K5: CUDA-core pair kernels (FP32 / FP64 Z), tiles [t0, t1) of the
 // paper's triangular tile order.

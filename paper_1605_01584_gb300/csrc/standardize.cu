@@ -168,18 +168,17 @@ __device__ __forceinline__ float4 load4(const float* x, int64_t k) {
   }
 }
 
+// The rows of one matrix, warps warp0, warp0 + nwarps, ... of a launch.
 template <int MODE, bool ALIGNED>
-__global__ void __launch_bounds__(256)
-    k_standardize_f32v(const float* __restrict__ X, int64_t n, int64_t l,
-                       int64_t ldx, int64_t lpad, double inv_l, float zscale,
-                       void* __restrict__ out0, void* __restrict__ out1,
-                       uint8_t* __restrict__ flags) {
+__device__ __forceinline__ void standardize_rows_f32v(
+    const float* __restrict__ X, int64_t n, int64_t l, int64_t ldx,
+    int64_t lpad, double inv_l, float zscale, void* __restrict__ out0,
+    void* __restrict__ out1, uint8_t* __restrict__ flags, int64_t warp0,
+    int64_t nwarps) {
   // a warp standardizes 4 rows at a time, 8 lanes per row: the per-row
   // FP64 work (3 reduction steps, mean, 1/sqrt) is shared by 4 rows
   const int lane = threadIdx.x & 31;
   const int grp = lane >> 3, gl = lane & 7;
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t l4 = l & ~int64_t(3);
   for (int64_t i0 = 4 * warp0; i0 < n; i0 += 4 * nwarps) {
     const int64_t i = i0 + grp;
@@ -284,6 +283,52 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <int MODE, bool ALIGNED>
+__global__ void __launch_bounds__(256)
+    k_standardize_f32v(const float* __restrict__ X, int64_t n, int64_t l,
+                       int64_t ldx, int64_t lpad, double inv_l, float zscale,
+                       void* __restrict__ out0, void* __restrict__ out1,
+                       uint8_t* __restrict__ flags) {
+  standardize_rows_f32v<MODE, ALIGNED>(
+      X, n, l, ldx, lpad, inv_l, zscale, out0, out1, flags,
+      ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+      ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// Many matrices in one launch: block row y standardizes matrix y of the
+// table (its rows in a grid-stride loop over blockIdx.x), with the same
+// arithmetic as the one-matrix launch.
+struct StdItem {
+  const float* X;
+  int64_t n, l, ldx, lpad;
+  double inv_l;
+  float zscale;
+  int aligned;
+  void* out0;
+  void* out1;
+  uint8_t* flags;
+};
+
+struct StdTable {
+  StdItem it[kStdBatchMax];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+    k_standardize_batched(const __grid_constant__ StdTable t) {
+  const StdItem& d = t.it[blockIdx.y];
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (d.aligned)
+    standardize_rows_f32v<MODE, true>(d.X, d.n, d.l, d.ldx, d.lpad, d.inv_l,
+                                      d.zscale, d.out0, d.out1, d.flags, w0,
+                                      nw);
+  else
+    standardize_rows_f32v<MODE, false>(d.X, d.n, d.l, d.ldx, d.lpad, d.inv_l,
+                                       d.zscale, d.out0, d.out1, d.flags, w0,
+                                       nw);
+}
+
 template <int MODE>
 void launch_f32v(const float* X, int64_t ldx, pcc_zmat* Z, int blocks,
                  float zscale, void* o0, void* o1, cudaStream_t s) {
@@ -365,6 +410,75 @@ cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
   if (xt == PCC_F64)
     return launch_mode(reinterpret_cast<const double*>(X), ldx, Z, s);
   return launch_mode(reinterpret_cast<const float*>(X), ldx, Z, s);
+}
+
+cudaError_t launch_standardize_batched(const float* const* Xs,
+                                       const int64_t* ldxs, pcc_zmat* const* Zs,
+                                       int count, cudaStream_t s) {
+  // one launch per stored form; the FP64 form has no FP32 row loop here
+  const pcc_prec forms[4] = {PCC_PREC_BF16X3, PCC_PREC_FP16X3S,
+                             PCC_PREC_BF16X1, PCC_PREC_FP32};
+  for (int f = 0; f < 4; ++f) {
+    int b = 0;
+    while (b < count) {
+      StdTable t;
+      int c = 0;
+      int64_t nmax = 0;
+      for (; b < count && c < kStdBatchMax; ++b) {
+        pcc_zmat* Z = Zs[b];
+        const pcc_prec zp =
+            Z->prec == PCC_PREC_BF16X4 ? PCC_PREC_BF16X3 : Z->prec;
+        if (zp != forms[f]) continue;
+        StdItem& d = t.it[c++];
+        d.X = Xs[b];
+        d.n = Z->n;
+        d.l = Z->l;
+        d.ldx = ldxs[b];
+        d.lpad = Z->lpad;
+        d.inv_l = 1.0 / (double)Z->l;
+        d.zscale = forms[f] == PCC_PREC_FP16X3S
+                       ? (float)ldexp(1.0, Z->scale_exp)
+                       : 1.f;
+        d.aligned = (ldxs[b] % 4) == 0 &&
+                    (reinterpret_cast<uintptr_t>(Xs[b]) & 15) == 0;
+        d.out0 = forms[f] == PCC_PREC_FP32 ? Z->z : Z->hi;
+        d.out1 = (forms[f] == PCC_PREC_BF16X3 || forms[f] == PCC_PREC_FP16X3S)
+                     ? Z->lo
+                     : nullptr;
+        d.flags = Z->flags;
+        if (Z->n > nmax) nmax = Z->n;
+      }
+      if (c == 0) continue;
+      // 32 rows per block and sweep; at most 8 blocks per SM per matrix
+      int64_t bx = (nmax + 31) / 32;
+      const int64_t cap = (int64_t)num_sms(Zs[0]->device) * 8;
+      if (bx > cap) bx = cap;
+      const dim3 grid((unsigned)bx, (unsigned)c, 1);
+      switch (forms[f]) {
+        case PCC_PREC_BF16X3:
+          k_standardize_batched<M_BF16X3><<<grid, 256, 0, s>>>(t);
+          break;
+        case PCC_PREC_FP16X3S:
+          k_standardize_batched<M_FP16X3S><<<grid, 256, 0, s>>>(t);
+          break;
+        case PCC_PREC_BF16X1:
+          k_standardize_batched<M_BF16X1><<<grid, 256, 0, s>>>(t);
+          break;
+        default:
+          k_standardize_batched<M_FP32><<<grid, 256, 0, s>>>(t);
+          break;
+      }
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  // FP64 outputs: one launch each
+  for (int b = 0; b < count; ++b)
+    if (Zs[b]->prec == PCC_PREC_FP64) {
+      cudaError_t e = launch_standardize(Xs[b], PCC_F32, ldxs[b], Zs[b], s);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 }  // namespace pcc

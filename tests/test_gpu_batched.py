@@ -151,3 +151,78 @@ def test_batched_pair_mma_equals_single_ctas(pcc_gpu):
         ok = ~np.isnan(got)
         assert np.array_equal(got[ok].view(np.uint32),
                               ref[b][ok].view(np.uint32)), b
+
+
+def _zbytes(pcc, Z):
+    """The stored halves (or z) and flags of Z as raw bytes on the host."""
+    import ctypes
+    torch = _torch()
+    info, buf = Z.info(), Z.buffers()
+    n, lpad = info["n"], info["lpad"]
+    libcuda = ctypes.CDLL("libcuda.so.1")
+    out = {}
+    for key, per in (("hi", 2), ("lo", 2), ("z", 4 if info["prec"] == 1
+                                            else 8), ("flags", 0)):
+        if not buf[key]:
+            continue
+        nb = n if key == "flags" else n * lpad * per
+        t = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        assert libcuda.cuMemcpy(ctypes.c_uint64(t.data_ptr()),
+                                ctypes.c_uint64(buf[key]),
+                                ctypes.c_size_t(nb)) == 0
+        out[key] = t.cpu().numpy()
+    return out
+
+
+def test_standardize_batched_equals_single_calls(pcc_gpu):
+    """One launch per stored form over many matrices (uneven n and l, an
+    odd row pitch, AUTO resolving to FP16X3S and BF16X3 by l) gives the
+    bits of one pcc_standardize per matrix, reuses matching Zmats and
+    replaces one whose shape changed."""
+    torch = _torch()
+    pcc = pcc_gpu
+    shapes = [(500, 40), (3, 5), (2049, 129), (700, 2100), (130, 1000),
+              (1000, 513), (64, 64), (4000, 300)]
+    Xs = []
+    for b, (n, l) in enumerate(shapes):
+        X = synth.counts_log(n, l, 700 + b)
+        X[n // 2] = 3.0  # flagged row
+        if b == 5:  # odd pitch: rows not 16-byte aligned
+            wide = np.zeros((n, l + 1), dtype=np.float32)
+            wide[:, :l] = X
+            Xs.append(torch.from_numpy(wide).cuda()[:, :l])
+        else:
+            Xs.append(torch.from_numpy(X).cuda())
+    for prec in ("auto", "bf16x3", "bf16x1", "fp32", "fp64"):
+        Zb = pcc.pcc_standardize_batched(Xs, prec)
+        for b, X in enumerate(Xs):
+            Zs = pcc.pcc_standardize(X, prec)
+            assert Zb[b].info() == Zs.info(), (prec, b)
+            got, want = _zbytes(pcc, Zb[b]), _zbytes(pcc, Zs)
+            assert got.keys() == want.keys()
+            for k in want:
+                assert np.array_equal(got[k], want[k]), (prec, b, k)
+            Zs.close()
+        # a second call reuses every matching Zmat in place
+        again = pcc.pcc_standardize_batched(Xs, prec, Zs=Zb)
+        assert all(a is z for a, z in zip(again, Zb))
+    Zb = pcc.pcc_standardize_batched(Xs, "auto")
+    auto = {b: Zb[b].info()["prec"] for b in range(len(shapes))}
+    assert auto[3] == 2 and auto[0] == 3  # BF16X3 above l = 2048
+    X2 = list(Xs)
+    X2[0] = torch.from_numpy(synth.counts_log(600, 40, 9)).cuda()
+    Zc = pcc.pcc_standardize_batched(X2, "auto", Zs=Zb)
+    assert Zc[0] is not Zb[0] and Zc[0].info()["n"] == 600
+    assert all(Zc[b] is Zb[b] for b in range(1, len(shapes)))
+
+
+def test_standardize_batched_invalid_arguments(pcc_gpu):
+    torch = _torch()
+    pcc = pcc_gpu
+    good = torch.rand((10, 8), device="cuda")
+    bad = torch.rand((1, 8), device="cuda")  # n < 2
+    with pytest.raises(pcc.PccError):
+        pcc.pcc_standardize_batched([good, bad])
+    with pytest.raises(pcc.PccError):
+        pcc.pcc_standardize_batched([])
