@@ -56,7 +56,8 @@ struct alignas(64) MatDesc {
   int64_t m;          // super-tiles per side
   int nkb;            // K blocks of 32
   int nprod;          // 4, 3 or 1 products per K step
-  int kalt;           // even/odd K blocks in two accumulators (long rows)
+  int kalt;           // the two halves of the K blocks in two accumulators
+                      // (long rows)
   uint32_t idesc;     // MMA instruction descriptor (BF16 or FP16 halves)
   float scale;        // accumulator -> r
   const uint8_t* flags;
@@ -251,17 +252,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t idesc = d->idesc;
         if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
         const int acc0 = acc;
+        uint32_t aph1 = aphase;
         if (kalt) {
+          // the second half of the K blocks goes to the other buffer,
+          // awaited only there (as in tc_pairs.cu)
           acc ^= 1;
           if (acc == 0) aphase ^= 1u;
-          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
+          aph1 = aphase;
         }
         tc_fence_after();
         const uint32_t d_tmem0 = tmem_base + (uint32_t)(acc0 * kBN);
         const uint32_t d_tmem1 = tmem_base + (uint32_t)(acc * kBN);
+        const int khalf = kalt ? nkb / 2 : nkb;
         for (int kb = 0; kb < nkb; ++kb) {
-          const uint32_t d_tmem = (kalt && (kb & 1)) ? d_tmem1 : d_tmem0;
-          const uint32_t first = kalt ? (kb < 2) : (kb == 0);
+          if (kalt && kb == khalf) {
+            if (!mbar_wait(&tempty[acc], aph1 ^ 1u, w)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t d_tmem = (kalt && kb >= khalf) ? d_tmem1 : d_tmem0;
+          const uint32_t first = kb == 0 || kb == khalf;
           if (!mbar_wait(&full[stage], phase, w)) {
             ok = false;
             break;
@@ -358,24 +370,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t lane_off =
           ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
       const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
-      if (kalt)
-        epilogue_rows<true, false, true>(
-            t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo,
-            tmem_base + lane_off + (uint32_t)(acc * kBN));
-      else
-        epilogue_rows<true, false>(t_row, stg, lane, n, rbase, jw0, base0,
-                                   rflags, cfl, eo);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        if (PAIR && crank != 0) {  // released to the even CTA's MMA issuer
-          mbar_arrive_cluster(cluster_addr(&tempty[acc0], 0));
-          if (kalt) mbar_arrive_cluster(cluster_addr(&tempty[acc], 0));
-        } else {
-          mbar_arrive(&tempty[acc0]);
-          if (kalt) mbar_arrive(&tempty[acc]);
+      // release a TMEM buffer to the MMA issuer (PAIR: the even CTA's)
+      auto release = [&](int a) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR && crank != 0)
+            mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
+          else
+            mbar_arrive(&tempty[a]);
         }
+      };
+      uint32_t t_out = t_row;
+      if (kalt) {
+        // fold the first half's accumulator into the second's and free it
+        t_out = tmem_base + lane_off + (uint32_t)(acc * kBN);
+        fold_acc(t_row, t_out);
+        release(acc0);
       }
+      epilogue_rows<true, false>(t_out, stg, lane, n, rbase, jw0, base0,
+                                 rflags, cfl, eo);
+      release(kalt ? acc : acc0);
       acc ^= 1;
       if (acc == 0) aphase ^= 1u;
     }

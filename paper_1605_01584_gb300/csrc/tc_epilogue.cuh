@@ -17,9 +17,12 @@
 // Why two accumulators for long rows: the tensor cores' FP32 accumulation
 // rounds every update toward zero, so its error grows with the number of
 // updates into a large partial sum (measured: 1.2e-5 on |r| ~ 1 at l = 2048
-// with one accumulator, always toward smaller |r|).  Alternating K blocks
-// between two accumulators halves both the updates and the partial sum of
-// each, and their sum is formed here with round-to-nearest.
+// with one accumulator, always toward smaller |r|).  Giving each of two
+// accumulators half of the K blocks halves both the updates and the partial
+// sum of each, and their sum is formed with round-to-nearest: fold_acc adds
+// the first accumulator into the second in TMEM, so that the first buffer
+// is released (and the next unit's first half can run in it) before the
+// store pass over the second.
 #pragma once
 #include <stdint.h>
 
@@ -29,6 +32,25 @@
 namespace pcc {
 
 constexpr int kStagePad = 33;  // transpose row pitch (conflict-free)
+
+// second += first over one warp's 32 TMEM lanes x 128 columns (t_first,
+// t_second: lane quarter and first column of the warp), one FP32
+// round-to-nearest add per element, 16 columns at a time (few registers:
+// the epilogue runs at the 168-register cap of a 10-warp CTA).
+__device__ __forceinline__ void fold_acc(uint32_t t_first, uint32_t t_second) {
+#pragma unroll 1
+  for (int c = 0; c < 8; ++c) {
+    uint32_t a[16], b[16];
+    tmem_ld_32x32b_x16(t_first + (uint32_t)(c * 16), a);
+    tmem_ld_32x32b_x16(t_second + (uint32_t)(c * 16), b);
+    tmem_ld_wait();
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      b[t] = __float_as_uint(__uint_as_float(a[t]) + __uint_as_float(b[t]));
+    tmem_st_32x32b_x16(t_second + (uint32_t)(c * 16), b);
+  }
+  tmem_st_wait();
+}
 
 struct EpiOut {
   float* R;                    // packed output (or null)
@@ -40,20 +62,17 @@ struct EpiOut {
   int* status;
 };
 
-// t_row: TMEM address of (lane 32q, first column of the warp's 128); with
-// DUAL the accumulator is split over two TMEM buffers (even and odd K
-// blocks) and t_row2 addresses the second, summed here in FP32; stg: this
-// warp's 32 x kStagePad floats; rbase: first row; jw0: first column; base0 =
-// pair_row_base(n, rbase); rflags: bit rr = row rbase+rr flagged (or >= n);
-// cfl[c]: flag of column jw0 + 32c + lane; ncol, ldr: DENSE only.
-template <bool WRITE_R, bool EDGES, bool DUAL = false, bool DENSE = false>
+// t_row: TMEM address of (lane 32q, first column of the warp's 128); stg:
+// this warp's 32 x kStagePad floats; rbase: first row; jw0: first column;
+// base0 = pair_row_base(n, rbase); rflags: bit rr = row rbase+rr flagged (or
+// >= n); cfl[c]: flag of column jw0 + 32c + lane; ncol, ldr: DENSE only.
+template <bool WRITE_R, bool EDGES, bool DENSE = false>
 __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
                                               int lane, int64_t n,
                                               int64_t rbase, int64_t jw0,
                                               int64_t base0, uint32_t rflags,
                                               const int (&cfl)[4],
                                               const EpiOut& eo,
-                                              uint32_t t_row2 = 0,
                                               int64_t ncol = 0,
                                               int64_t ldr = 0) {
   if constexpr (!DENSE) ncol = n;
@@ -69,28 +88,16 @@ __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
     return c;
   };
   uint32_t v[32];
-  uint32_t v2[DUAL ? 32 : 1];
   int c = next_active(-1);
-  if (c < 4) {
-    tmem_ld_32x32b_x32(t_row + (uint32_t)(c * 32), v);
-    if constexpr (DUAL) tmem_ld_32x32b_x32(t_row2 + (uint32_t)(c * 32), v2);
-  }
+  if (c < 4) tmem_ld_32x32b_x32(t_row + (uint32_t)(c * 32), v);
   while (c < 4) {
     tmem_ld_wait();
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      float a = __uint_as_float(v[t]);
-      if constexpr (DUAL) a += __uint_as_float(v2[t]);
-      stg[lane * kStagePad + t] = a;
-    }
+    for (int t = 0; t < 32; ++t) stg[lane * kStagePad + t] = __uint_as_float(v[t]);
     __syncwarp();
     // the next block's TMEM load overlaps this block's stores
     const int cn = next_active(c);
-    if (cn < 4) {
-      tmem_ld_32x32b_x32(t_row + (uint32_t)(cn * 32), v);
-      if constexpr (DUAL)
-        tmem_ld_32x32b_x32(t_row2 + (uint32_t)(cn * 32), v2);
-    }
+    if (cn < 4) tmem_ld_32x32b_x32(t_row + (uint32_t)(cn * 32), v);
     const int64_t jc0 = jw0 + c * 32;
     const int64_t j = jc0 + lane;
     const bool cflag = cfl[c] != 0;

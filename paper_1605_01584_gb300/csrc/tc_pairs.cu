@@ -91,8 +91,8 @@ struct TcParams {
   int64_t u_begin;   // units [u_begin, u_end)
   int64_t u_end;
   int nkb;           // K blocks of KB
-  int kalt;          // 1: even/odd K blocks go to two accumulators (both
-                     // TMEM buffers) for long rows
+  int kalt;          // 1: the two halves of the K blocks go to two
+                     // accumulators (both TMEM buffers) for long rows
   float out_scale;   // 2^-2s for FP16X3S, else 1
   float tau;
   const uint8_t* flags;
@@ -346,19 +346,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (CL == 1 && row0 >= n) continue;
         if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
         const int acc0 = acc;
+        uint32_t aph1 = aphase;
         if (p.kalt) {
-          // a long-row unit also takes the other buffer of the ring
+          // a long-row unit also takes the other buffer of the ring, for
+          // the second half of its K blocks: that buffer is awaited only
+          // there, so the first half overlaps the previous unit's stores
           acc ^= 1;
           if (acc == 0) aphase ^= 1u;
-          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
+          aph1 = aphase;
         }
         tc_fence_after();
         const uint32_t d_tmem0 = tmem_base + (uint32_t)(acc0 * kBN);
         const uint32_t d_tmem1 = tmem_base + (uint32_t)(acc * kBN);
+        const int khalf = p.kalt ? p.nkb / 2 : p.nkb;
         bool ok = true;
         for (int kb = 0; kb < p.nkb; ++kb) {
-          const uint32_t d_tmem = (p.kalt && (kb & 1)) ? d_tmem1 : d_tmem0;
-          const uint32_t first = p.kalt ? (kb < 2) : (kb == 0);
+          if (p.kalt && kb == khalf) {
+            if (!mbar_wait(&tempty[acc], aph1 ^ 1u, w)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t d_tmem = (p.kalt && kb >= khalf) ? d_tmem1 : d_tmem0;
+          const uint32_t first = kb == 0 || kb == khalf;
           if (!mbar_wait(&full[stage], phase, w)) {
             ok = false;
             break;
@@ -466,26 +477,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
       const EpiOut eo{p.R, p.out_scale, p.tau, p.edges, p.count, p.cap,
                       p.status};
-      if (p.kalt)
-        epilogue_rows<WRITE_R, EDGES, true, CROSS>(
-            t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo,
-            tmem_base + lane_off + (uint32_t)(acc * kBN), p.ncol, p.ldr);
-      else
-        epilogue_rows<WRITE_R, EDGES, false, CROSS>(
-            t_row, stg, lane, n, rbase, jw0, base0, rflags, cfl, eo, 0,
-            p.ncol, p.ldr);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        if (PAIR && crank != 0) {
-          // the accumulator is released to the even CTA's MMA issuer
-          mbar_arrive_cluster(cluster_addr(&tempty[acc0], 0));
-          if (p.kalt) mbar_arrive_cluster(cluster_addr(&tempty[acc], 0));
-        } else {
-          mbar_arrive(&tempty[acc0]);
-          if (p.kalt) mbar_arrive(&tempty[acc]);
+      // release a TMEM buffer to the MMA issuer (PAIR: the even CTA's)
+      auto release = [&](int a) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR && crank != 0)
+            mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
+          else
+            mbar_arrive(&tempty[a]);
         }
+      };
+      uint32_t t_out = t_row;
+      if (p.kalt) {
+        // fold the first half's accumulator into the second's and free it
+        t_out = tmem_base + lane_off + (uint32_t)(acc * kBN);
+        fold_acc(t_row, t_out);
+        release(acc0);
       }
+      epilogue_rows<WRITE_R, EDGES, CROSS>(t_out, stg, lane, n, rbase, jw0,
+                                           base0, rflags, cfl, eo, p.ncol,
+                                           p.ldr);
+      release(p.kalt ? acc : acc0);
       acc ^= 1;
       if (acc == 0) aphase ^= 1u;
     }
