@@ -362,6 +362,20 @@ def run_gpu(args):
         out["fp32_simt"] = {"ms_per_step": ms32,
                             "value": gpair_samples(n, l) / (ms32 / 1e3),
                             "speedup_split_tc": ms32 / ms_step}
+        # its roofline: the FP32 FMA rate of the CUDA cores, measured by a
+        # microbenchmark (the driver's peaks hold no such number), beside
+        # the nominal SMs x 128 FP32 lanes x 2 flops x max SM clock
+        fma = pcc.pcc_measure_fp32_fma()
+        sms = torch.cuda.get_device_properties(
+            torch.cuda.current_device()).multi_processor_count
+        ach = alg_flops / (ms32 / 1e3) / 1e12
+        nominal = (sms * 128 * 2 * clk["sm_max_mhz"] * 1e6 / 1e12
+                   if clk.get("sm_max_mhz") else None)
+        out["fp32_simt"]["roofline"] = {
+            "bound": "alu", "achieved": ach, "peak": fma, "unit": "TFLOP/s",
+            "frac": ach / fma, "peak_kind": "measured FFMA microbenchmark",
+            "nominal_peak": nominal,
+            "note": "algorithmic 2l flops per pair over the whole FP32 step"}
         Z32.close()
 
     # end to end through the C ABI with host buffers

@@ -358,6 +358,15 @@ pcc_status pcc_get_tuning(int32_t *stage_k, int32_t *cluster,
                           int32_t *band_rows, double *cost_c0,
                           double *cost_c1);
 
+/* Measure the FP32 fused multiply-add rate of the current device's CUDA
+ * cores (TFLOP/s, 2 flops per FMA), the roofline of the CUDA-core pair
+ * kernels (the FP32 form is the comparison path of the split tensor-core
+ * forms).  Runs a kernel of independent FMA chains on `stream` (8 blocks of
+ * 256 threads per SM, best of three timed launches) and waits for it; it
+ * allocates nothing.  Errors: PCC_ERR_INVALID_ARG for a NULL tflops,
+ * PCC_ERR_CUDA.  The paper has no counterpart (a measurement helper). */
+pcc_status pcc_measure_fp32_fma(double *tflops, void *stream);
+
 /* Limit, in nanoseconds, of every pipeline wait inside the tensor-core
  * kernels (default 4e9).  A wait that runs out sets PCC_ERR_TIMEOUT in the
  * status word and the kernel returns early instead of hanging. */

@@ -115,6 +115,7 @@ def load(path: str | None = None):
                                  ctypes.c_double]),
         "pcc_get_tuning": (_ST, [_P, _P, _P, _P, _P]),
         "pcc_set_pair_mma": (_ST, [_I32]),
+        "pcc_measure_fp32_fma": (_ST, [_P, _P]),
         "pcc_get_pair_mma": (_I32, []),
         "pcc_num_pairs": (_I64, [_I64]),
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
@@ -446,6 +447,14 @@ def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,
            "pcc_set_tuning")
     if pair_mma is not None:
         _check(load().pcc_set_pair_mma(int(pair_mma)), "pcc_set_pair_mma")
+
+
+def pcc_measure_fp32_fma(stream=None) -> float:
+    """Measured FP32 FMA rate of the device's CUDA cores, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(load().pcc_measure_fp32_fma(ctypes.byref(v), _stream(stream)),
+           "pcc_measure_fp32_fma")
+    return v.value
 
 
 def pcc_get_tuning() -> dict:

@@ -1,0 +1,75 @@
+// fma_peak.cu -- the FP32 CUDA-core FMA rate of this device, measured.
+//
+// The CUDA-core pair kernels (simt_pairs.cu) are bound by FP32 (or FP64)
+// fused multiply-adds, so their roofline is the FMA rate of the SMs, which
+// the driver's peak measurements (a copy and a bf16 GEMM) do not give.
+// Every thread runs 8 independent FMA chains, enough to keep the FP32 pipes
+// busy, with a grid of 8 blocks of 256 threads per SM; the kernel touches
+// no memory but one word that keeps the compiler from dropping the chains.
+#include "pcc_internal.h"
+
+namespace pcc {
+namespace {
+
+__device__ float g_fma_sink;
+
+constexpr int kFmaChains = 8;
+
+__global__ void __launch_bounds__(256)
+    k_fma_chains(int iters, float a, float b) {
+  float x[kFmaChains];
+#pragma unroll
+  for (int c = 0; c < kFmaChains; ++c)
+    x[c] = (float)(threadIdx.x + c) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int c = 0; c < kFmaChains; ++c) x[c] = fmaf(x[c], a, b);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kFmaChains; ++c) s += x[c];
+  if (s == 1234.5f) g_fma_sink = s;  // never true for these inputs
+}
+
+}  // namespace
+}  // namespace pcc
+
+extern "C" pcc_status pcc_measure_fp32_fma(double* tflops, void* stream) {
+  using namespace pcc;
+  if (!tflops) return PCC_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PCC_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int blocks = num_sms(dev) * 8, threads = 256, iters = 2048;
+  // a = 1 - 2^-20, b = 2^-20: the chains stay bounded and never denormal
+  const float a = 0.99999905f, b = 9.5367432e-7f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return PCC_ERR_CUDA;
+  }
+  float best = 0.f;
+  cudaError_t err = cudaSuccess;
+  for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+    cudaEventRecord(e0, s);
+    k_fma_chains<<<blocks, threads, 0, s>>>(iters, a, b);
+    err = cudaGetLastError();
+    cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    // the first launch warms the clocks up and is not counted
+    if (err == cudaSuccess && rep > 0 && ms > 0.f && (best == 0.f || ms < best))
+      best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess || best <= 0.f) return PCC_ERR_CUDA;
+  const double flops = 2.0 * (double)blocks * threads * iters * 16.0 * kFmaChains;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  return PCC_OK;
+}
