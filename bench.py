@@ -183,6 +183,53 @@ def oracle_rate(X, seconds: float, seed: int = 11):
     return rate, oracle.num_threads(), sample
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True,
+                             timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_single_thread_rate(l: int, seconds: float = 2.0):
+    """The oracle's rate on one host thread (a child process started with
+    OMP_NUM_THREADS=1, random pairs of a 4,096-row matrix of the same row
+    length: the cost per pair*sample depends only on l)."""
+    code = (
+        "import sys, time, numpy as np\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import oracle, synth\n"
+        f"X = synth.counts_log(4096, {l}, 3).astype(np.float64)\n"
+        "rng = np.random.default_rng(7); n = 4096; npairs = 2000\n"
+        "while True:\n"
+        "    I = rng.integers(0, n, npairs); J = rng.integers(0, n, npairs)\n"
+        "    t0 = time.perf_counter(); oracle.pcc_pairs(X, I, J)\n"
+        "    dt = time.perf_counter() - t0\n"
+        f"    if dt >= {seconds} or npairs >= 1 << 26: break\n"
+        "    npairs *= 4\n"
+        f"print(npairs * {l} / dt / 1e9, oracle.num_threads())\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True,
+                           text=True, env=env, timeout=120)
+        v, th = r.stdout.split()[:2]
+        return float(v) if int(th) == 1 else None
+    except Exception:
+        return None
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -206,7 +253,8 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "n": N_GENES, "l": L_SAMPLES,
                    "tau": TAU, "seed": SEED},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -428,7 +476,10 @@ def run_gpu(args):
     if rank == 0 and not args.skip_cpu:
         v, cores, sample = oracle_rate(X, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores,
-                               "kind": "oracle", "sample": sample}
+                               "kind": "oracle", "sample": sample,
+                               "cpu_model": cpu_model(),
+                               "single_thread_value":
+                                   oracle_single_thread_rate(l)}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
