@@ -44,6 +44,12 @@ bool is_split(pcc_prec p);
 // PCC_PREC_AUTO -> the split form for rows of length l; others unchanged
 pcc_prec resolve_prec(pcc_prec p, int64_t l);
 int num_sms(int device);
+// Per-device slot of a small cache (devices 0 .. kDeviceSlots-1; larger ids
+// share the last slot).
+constexpr int kDeviceSlots = 64;
+inline int device_slot(int device) {
+  return device < 0 ? 0 : (device < kDeviceSlots ? device : kDeviceSlots - 1);
+}
 uint64_t wait_limit_ns();
 bool debug_drop_loads();  // test hook of pcc_debug_drop_loads
 cudaError_t ensure_func_smem(const void* func, int bytes);

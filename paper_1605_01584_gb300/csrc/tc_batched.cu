@@ -440,7 +440,8 @@ std::vector<Plan*> g_plans;  // small cache, most recent last
 
 // CTA pairs of the pair form that can be resident at once
 int pair_workers(int device) {
-  static int mc = 0;
+  static int mc_of[kDeviceSlots] = {};
+  int& mc = mc_of[device_slot(device)];
   if (mc == 0) {
     auto fn = k_pairs_tc_batched<true>;
     const int smem = BCfg<true>::kSmemBytes;

@@ -559,8 +559,9 @@ cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int max_clusters_of[2] = {0, 0};  // per form, per instance
-    int& max_clusters = max_clusters_of[pair ? 1 : 0];
+    // per template instance, form and device
+    static int max_clusters_of[2][kDeviceSlots] = {};
+    int& max_clusters = max_clusters_of[pair ? 1 : 0][device_slot(Z->device)];
     if (max_clusters == 0) {
       cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
       int mc = 0;

@@ -705,7 +705,8 @@ cudaError_t launch_perm_kernel(const pcc_zmat* Z, const CUtensorMap& ph,
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int max_clusters = 0;  // per template instance
+    static int max_clusters_of[kDeviceSlots] = {};  // per instance, device
+    int& max_clusters = max_clusters_of[device_slot(Z->device)];
     if (max_clusters == 0) {
       cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
       int mc = 0;
