@@ -15,9 +15,11 @@ def _torch():
     return torch
 
 
+# (300, 1100) and (260, 2100): rows past 1,024 samples, two accumulators
 SHAPES = [(3, 5, "fp16x3s"), (200, 2, "bf16x3"), (513, 33, "fp16x3s"),
           (300, 300, "bf16x3"), (1000, 64, "bf16x1"), (2049, 129, "fp16x3s"),
-          (130, 1000, "fp16x3s"), (700, 200, "bf16x4")]
+          (130, 1000, "fp16x3s"), (700, 200, "bf16x4"), (300, 1100, "fp16x3s"),
+          (260, 2100, "bf16x3")]
 
 
 def _setup(pcc, shapes, seed0=900):
