@@ -174,9 +174,10 @@ def oracle_rate(X, seconds: float, seed: int = 11):
         t0 = time.perf_counter()
         oracle.pcc_pairs(X64, I, J)
         dt = time.perf_counter() - t0
-        if dt >= seconds or npairs >= 1 << 28:
+        if dt >= 0.9 * seconds or npairs >= 1 << 28:
             break
-        npairs = int(npairs * min(max(seconds / max(dt, 1e-3), 2.0), 64.0))
+        # grow toward the target; the last round lands on it
+        npairs = int(npairs * min(max(seconds / max(dt, 1e-3), 1.1), 64.0))
     rate = npairs * l / dt / 1e9
     sample = (f"{npairs} random pairs (i,j) of the {n}x{l} matrix, Eq. (1) "
               f"in FP64 with per-row mean/SSQ, {dt:.1f} s")
