@@ -323,7 +323,8 @@ pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
 /* Knobs of the tensor-core kernels, as chosen by the tuner
  * (paper_1605_01584_gb300/autotune.py); they affect later launches only and
  * never the result.  0 (or <= 0 for the costs) keeps a value.
- *   stage_k    K per shared-memory ring stage: 32 (4 stages) or 64 (2).
+ *   stage_k    K per shared-memory ring stage: 32 (4 stages; 6 in the 2-SM
+ *              pair form, whose stages are a third smaller) or 64 (2).
  *   cluster    2 = CTA pairs that share the column operand by TMA
  *              multicast, 1 = independent CTAs.
  *   band_rows  super-tile rows per band of the pair schedule (rows of a

@@ -1,7 +1,8 @@
 """Tuner for the tensor-core kernels' knobs (pcc_set_tuning).
 
 The knobs never change results, only speed:
-  stage_k    K per shared-memory ring stage (32: 4 stages, 64: 2 stages)
+  stage_k    K per shared-memory ring stage (32: 4 stages, 6 in the 2-SM
+             pair form; 64: 2 stages)
   cluster    2 = CTA pairs sharing the column operand by TMA multicast,
              1 = independent CTAs
   pair_mma   with CTA pairs and stage_k 32: 1 = one 2-SM MMA per pair
