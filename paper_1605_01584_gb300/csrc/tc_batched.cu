@@ -49,7 +49,9 @@ struct BCfg {
   static_assert(kSmemBytes <= 232448, "shared memory budget");
 };
 
-struct alignas(64) MatDesc {
+// takes the 128-byte alignment of its tensor maps (TMA reads them from
+// global memory)
+struct MatDesc {
   CUtensorMap tm_hi;  // box 32 x 128, 64-B swizzle
   CUtensorMap tm_lo;
   int64_t n;
