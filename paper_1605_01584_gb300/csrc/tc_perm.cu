@@ -125,15 +125,17 @@ struct PCfg {
 // One block per (permutation, group of rows).  The permutation is checked
 // and staged in shared memory; with NG > 0 each lane then keeps the indices
 // of its NG groups of 8 outputs in registers for all the block's rows (rows
-// up to 256 * NG samples).  Each warp takes one row at a time and stages it
-// in shared memory with hi and lo interleaved (word s = hi[s] | lo[s] << 16),
+// up to 256 * NG samples).  Each warp takes RR rows at a time and stages
+// them in shared memory with hi and lo interleaved (word s = hi[s] |
+// lo[s] << 16),
 // so one 4-byte read fetches both halves of a sample; every lane then
 // writes 8 permuted elements of each half with one 16-byte store per half
 // (lpad is a multiple of 64, so rows split into whole 8-element groups).
-// Shared memory: 4 * lpad bytes of indices and 4 * lpad per warp.
+// Shared memory: 4 * lpad bytes of indices and 4 * lpad per row a warp
+// stages (two rows at a time for rows up to 1,024 samples, else one).
 constexpr int kGatherWarps = 8;
 
-template <int NG>
+template <int NG, int RR>
 __global__ void __launch_bounds__(kGatherWarps * 32)
     k_perm_gather(const uint16_t* __restrict__ hi,
                   const uint16_t* __restrict__ lo,
@@ -169,45 +171,55 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
       for (int t = 0; t < 8; ++t) idx[8 * g + t] = v < ngroups ? pi[v * 8 + t] : -1;
     }
   }
-  uint32_t* wrow = rows + (size_t)warp * lpad;  // one row, hi | lo << 16
+  // RR rows per warp and iteration (rows j, j + W, ...), staged together so
+  // that their loads are in flight at once
+  uint32_t* wrow = rows + (size_t)warp * RR * lpad;  // hi | lo << 16
   const int64_t j0 = blockIdx.x * rows_per_block;
   const int64_t j1 = j0 + rows_per_block < n ? j0 + rows_per_block : n;
-  for (int64_t j = j0 + warp; j < j1; j += kGatherWarps) {
-    const uint4* gh = reinterpret_cast<const uint4*>(hi + j * lpad);
-    const uint4* gl = reinterpret_cast<const uint4*>(lo + j * lpad);
-    uint4* sw = reinterpret_cast<uint4*>(wrow);
+  for (int64_t j = j0 + warp; j < j1; j += RR * kGatherWarps) {
     for (int64_t v = lane; v < ngroups; v += 32) {
-      const uint4 a = gh[v], b = gl[v];  // samples 8v .. 8v+7
-      uint4 w0, w1;
-      w0.x = (a.x & 0xFFFFu) | (b.x << 16);
-      w0.y = (a.x >> 16) | (b.x & 0xFFFF0000u);
-      w0.z = (a.y & 0xFFFFu) | (b.y << 16);
-      w0.w = (a.y >> 16) | (b.y & 0xFFFF0000u);
-      w1.x = (a.z & 0xFFFFu) | (b.z << 16);
-      w1.y = (a.z >> 16) | (b.z & 0xFFFF0000u);
-      w1.z = (a.w & 0xFFFFu) | (b.w << 16);
-      w1.w = (a.w >> 16) | (b.w & 0xFFFF0000u);
-      sw[2 * v] = w0;
-      sw[2 * v + 1] = w1;
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const int64_t jr = j + r * kGatherWarps;
+        if (jr >= j1) break;
+        const uint4 a = reinterpret_cast<const uint4*>(hi + jr * lpad)[v];
+        const uint4 b = reinterpret_cast<const uint4*>(lo + jr * lpad)[v];
+        uint4 w0, w1;  // samples 8v .. 8v+7, interleaved
+        w0.x = (a.x & 0xFFFFu) | (b.x << 16);
+        w0.y = (a.x >> 16) | (b.x & 0xFFFF0000u);
+        w0.z = (a.y & 0xFFFFu) | (b.y << 16);
+        w0.w = (a.y >> 16) | (b.y & 0xFFFF0000u);
+        w1.x = (a.z & 0xFFFFu) | (b.z << 16);
+        w1.y = (a.z >> 16) | (b.z & 0xFFFF0000u);
+        w1.z = (a.w & 0xFFFFu) | (b.w << 16);
+        w1.w = (a.w >> 16) | (b.w & 0xFFFF0000u);
+        uint4* sw = reinterpret_cast<uint4*>(wrow + r * lpad);
+        sw[2 * v] = w0;
+        sw[2 * v + 1] = w1;
+      }
     }
     __syncwarp();
-    uint4* oh = reinterpret_cast<uint4*>(ohi + (kk * n + j) * lpad);
-    uint4* ol = reinterpret_cast<uint4*>(olo + (kk * n + j) * lpad);
     auto emit = [&](int64_t v, const int32_t* q) {
-      uint32_t wv[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) wv[t] = q[t] >= 0 ? wrow[q[t]] : 0u;
-      uint4 ua, ub;  // hi: low halves, lo: high halves
-      ua.x = (wv[0] & 0xFFFFu) | (wv[1] << 16);
-      ua.y = (wv[2] & 0xFFFFu) | (wv[3] << 16);
-      ua.z = (wv[4] & 0xFFFFu) | (wv[5] << 16);
-      ua.w = (wv[6] & 0xFFFFu) | (wv[7] << 16);
-      ub.x = (wv[0] >> 16) | (wv[1] & 0xFFFF0000u);
-      ub.y = (wv[2] >> 16) | (wv[3] & 0xFFFF0000u);
-      ub.z = (wv[4] >> 16) | (wv[5] & 0xFFFF0000u);
-      ub.w = (wv[6] >> 16) | (wv[7] & 0xFFFF0000u);
-      oh[v] = ua;
-      ol[v] = ub;
+      for (int r = 0; r < RR; ++r) {
+        const int64_t jr = j + r * kGatherWarps;
+        if (jr >= j1) break;
+        const uint32_t* w = wrow + r * lpad;
+        uint32_t wv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) wv[t] = q[t] >= 0 ? w[q[t]] : 0u;
+        uint4 ua, ub;  // hi: low halves, lo: high halves
+        ua.x = (wv[0] & 0xFFFFu) | (wv[1] << 16);
+        ua.y = (wv[2] & 0xFFFFu) | (wv[3] << 16);
+        ua.z = (wv[4] & 0xFFFFu) | (wv[5] << 16);
+        ua.w = (wv[6] & 0xFFFFu) | (wv[7] << 16);
+        ub.x = (wv[0] >> 16) | (wv[1] & 0xFFFF0000u);
+        ub.y = (wv[2] >> 16) | (wv[3] & 0xFFFF0000u);
+        ub.z = (wv[4] >> 16) | (wv[5] & 0xFFFF0000u);
+        ub.w = (wv[6] >> 16) | (wv[7] & 0xFFFF0000u);
+        reinterpret_cast<uint4*>(ohi + (kk * n + jr) * lpad)[v] = ua;
+        reinterpret_cast<uint4*>(olo + (kk * n + jr) * lpad)[v] = ub;
+      }
     };
     if constexpr (NG > 0) {
 #pragma unroll
@@ -239,10 +251,11 @@ cudaError_t launch_gather(dim3 g, size_t gsmem, cudaStream_t s,
                                             rpb, ohi, olo, status);
     return cudaGetLastError();
   };
-  if (need <= 1) return go(k_perm_gather<1>);
-  if (need <= 2) return go(k_perm_gather<2>);
-  if (need <= 4) return go(k_perm_gather<4>);
-  return go(k_perm_gather<0>);
+  // two rows per warp while their staging stays small (rows up to 1,024)
+  if (need <= 1) return go(k_perm_gather<1, 2>);
+  if (need <= 2) return go(k_perm_gather<2, 2>);
+  if (need <= 4) return go(k_perm_gather<4, 2>);
+  return go(k_perm_gather<0, 1>);
 }
 
 template <bool BF16, bool RESA, bool PAIR>
@@ -783,7 +796,9 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     // gather the permuted halves of the batch
     const int64_t rpb = 64;
     dim3 g((unsigned)((n + rpb - 1) / rpb), (unsigned)kbatch, 1);
-    const size_t gsmem = (size_t)lpad * 4 + (size_t)kGatherWarps * 4 * lpad;
+    const size_t rr = lpad <= 1024 ? 2 : 1;  // rows staged per warp
+    const size_t gsmem =
+        (size_t)lpad * 4 + (size_t)kGatherWarps * rr * 4 * (size_t)lpad;
     e = launch_gather(g, gsmem, s, static_cast<const uint16_t*>(Z->hi),
                       static_cast<const uint16_t*>(Z->lo), d_perms, n, Z->l,
                       lpad, kb0, rpb, wh, wl, Z->status);
