@@ -504,6 +504,24 @@ def _timed(fn, steps, warmup, stream):
     return a.elapsed_time(b) / steps
 
 
+def _graph_timed(fn, steps, warmup):
+    """Run `warmup` plain steps (they allocate whatever a first call
+    allocates), capture one step in a CUDA graph and time `steps` replays;
+    None when the step cannot be captured."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+    except Exception:
+        torch.cuda.synchronize()
+        return None
+    return _timed(g.replay, steps, 1, torch.cuda.current_stream())
+
+
 def run_perm(args):
     """Permutation test workload: n=4096 x l=256, P=1000 seeded Fisher-Yates
     permutations, counts of |r_k| >= |r_obs| for every pair."""
@@ -525,7 +543,11 @@ def run_perm(args):
         cnt.zero_()
         pcc.pcc_perm_test(Z, dp, P, 0, P, cnt)
 
-    ms = _timed(step, max(3, min(args.steps, 20)), args.warmup, stream)
+    ms_stream = _timed(step, max(3, min(args.steps, 20)), args.warmup, stream)
+    # the whole test (standardize, count reset, gather, pair kernel) as one
+    # CUDA graph
+    ms_graph = _graph_timed(step, max(3, min(args.steps, 20)), 1)
+    ms = ms_graph if ms_graph is not None else ms_stream
     st = pcc.pcc_sync_status(Z)
     info = Z.info()
     tiles = (-(-n // 128)) * (-(-n // 128) + 1) // 2
@@ -534,6 +556,7 @@ def run_perm(args):
     out = {"metric": "permutation-test Gpair*samples*perms/s",
            "value": n * (n - 1) / 2 * l * P / (ms / 1e3) / 1e9,
            "unit": "Gpair*samples*perms/s", "ms_per_step": ms,
+           "ms_per_step_stream": ms_stream, "graph": ms_graph is not None,
            "steps": max(3, min(args.steps, 20)), "warmup": args.warmup,
            "status": st, "dtype": FORMS[info["prec"]][2],
            "config": {"workload": f"permutation test n=4096 x l=256, P={P}",
@@ -571,7 +594,11 @@ def run_batched(args):
         pcc.pcc_standardize_batched(Xs, args.prec, Zs=Zs)
         pcc.pcc_allpairs_upper_batched(Zs, Rs)
 
-    ms = _timed(step, max(3, min(args.steps, 10)), args.warmup, stream)
+    ms_stream = _timed(step, max(3, min(args.steps, 10)), args.warmup, stream)
+    # the whole step (one standardize launch per form, one pair launch) as
+    # one CUDA graph
+    ms_graph = _graph_timed(step, max(3, min(args.steps, 10)), 1)
+    ms = ms_graph if ms_graph is not None else ms_stream
 
     def kern():
         pcc.pcc_allpairs_upper_batched(Zs, Rs)
@@ -592,6 +619,7 @@ def run_batched(args):
                        info["lpad"] * m * (m + 1) / 2)
     out = {"metric": "batched all-pairs Gpair*samples/s", "value": work /
            (ms / 1e3), "unit": "Gpair*samples/s", "ms_per_step": ms,
+           "ms_per_step_stream": ms_stream, "graph": ms_graph is not None,
            "ms_batched_kernel": ms_k, "status": st,
            "config": {"workload": "64 uneven matrices n~U{500..20000}, "
                       "l~U{32..2048}", "split": args.prec,
