@@ -69,7 +69,8 @@ extern "C" pcc_status pcc_measure_fp32_fma(double* tflops, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess || best <= 0.f) return PCC_ERR_CUDA;
-  const double flops = 2.0 * (double)blocks * threads * iters * 16.0 * kFmaChains;
+  const double flops =
+      2.0 * (double)blocks * threads * iters * 16.0 * kFmaChains;
   *tflops = flops / (best * 1e-3) / 1e12;
   return PCC_OK;
 }

@@ -200,28 +200,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                                pol);
               tma_load_2d_pair(sB_lo(stage), &d->tm_lo, fb, kc, brow, pol);
             }
-            issued_mask |= 1u << stage;
-            last_phase[stage] = phase;
-            if (++stage == kStages) {
-              stage = 0;
-              phase ^= 1u;
-            }
-            continue;
-          }
-          mbar_arrive_expect_tx(&full[stage], bytes);
-          tma_load_2d_hint(sA_hi(stage), &d->tm_hi, &full[stage], kc,
-                           (int)row0, pol);
-          tma_load_2d_hint(sB_hi(stage), &d->tm_hi, &full[stage], kc,
-                           (int)col0, pol);
-          tma_load_2d_hint(sB_hi(stage) + kTileA, &d->tm_hi, &full[stage], kc,
-                           (int)col0 + kBM, pol);
-          if (nprod >= 3) {
-            tma_load_2d_hint(sA_lo(stage), &d->tm_lo, &full[stage], kc,
+          } else {
+            mbar_arrive_expect_tx(&full[stage], bytes);
+            tma_load_2d_hint(sA_hi(stage), &d->tm_hi, &full[stage], kc,
                              (int)row0, pol);
-            tma_load_2d_hint(sB_lo(stage), &d->tm_lo, &full[stage], kc,
+            tma_load_2d_hint(sB_hi(stage), &d->tm_hi, &full[stage], kc,
                              (int)col0, pol);
-            tma_load_2d_hint(sB_lo(stage) + kTileA, &d->tm_lo, &full[stage],
-                             kc, (int)col0 + kBM, pol);
+            tma_load_2d_hint(sB_hi(stage) + kTileA, &d->tm_hi, &full[stage], kc,
+                             (int)col0 + kBM, pol);
+            if (nprod >= 3) {
+              tma_load_2d_hint(sA_lo(stage), &d->tm_lo, &full[stage], kc,
+                               (int)row0, pol);
+              tma_load_2d_hint(sB_lo(stage), &d->tm_lo, &full[stage], kc,
+                               (int)col0, pol);
+              tma_load_2d_hint(sB_lo(stage) + kTileA, &d->tm_lo, &full[stage],
+                               kc, (int)col0 + kBM, pol);
+            }
           }
           issued_mask |= 1u << stage;
           last_phase[stage] = phase;

@@ -93,7 +93,8 @@ __device__ __forceinline__ void epilogue_rows(uint32_t t_row, float* stg,
   while (c < 4) {
     tmem_ld_wait();
 #pragma unroll
-    for (int t = 0; t < 32; ++t) stg[lane * kStagePad + t] = __uint_as_float(v[t]);
+    for (int t = 0; t < 32; ++t)
+      stg[lane * kStagePad + t] = __uint_as_float(v[t]);
     __syncwarp();
     // the next block's TMEM load overlaps this block's stores
     const int cn = next_active(c);

@@ -273,43 +273,37 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_load_2d_pair(sA_lo(stage), &tm_lo, fb, kc, (int)row0, pol);
               tma_load_2d_pair(sB_lo(stage), mb_lo, fb, kc, brow, pol);
             }
-            issued_mask |= 1u << stage;
-            last_phase[stage] = phase;
-            if (++stage == S) {
-              stage = 0;
-              phase ^= 1u;
-            }
-            continue;
-          }
-          mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
-          // Z is re-read by many tiles: keep it in L2 ahead of the
-          // evict-first output stream
-          tma_load_2d_hint(sA_hi(stage), &tm_hi, &full[stage], kc, (int)row0,
-                           pol);
-          if constexpr (CL == 1) {
-            tma_load_2d_hint(sB_hi(stage), mb_hi, &full[stage], kc,
-                             (int)col0, pol);
-            tma_load_2d_hint(sB_hi(stage) + kTileA, mb_hi, &full[stage], kc,
-                             (int)col0 + kBM, pol);
           } else {
-            // both CTAs need all 256 B rows: each loads its 128 and
-            // multicasts them to the pair
-            tma_load_2d_mc(sB_hi(stage) + crank * kTileA, mb_hi,
-                           &full[stage], kc, (int)(col0 + crank * kBM), 3,
-                           pol);
-          }
-          if (NPROD > 1) {
-            tma_load_2d_hint(sA_lo(stage), &tm_lo, &full[stage], kc,
+            mbar_arrive_expect_tx(&full[stage], C::kStageBytes);
+            // Z is re-read by many tiles: keep it in L2 ahead of the
+            // evict-first output stream
+            tma_load_2d_hint(sA_hi(stage), &tm_hi, &full[stage], kc,
                              (int)row0, pol);
             if constexpr (CL == 1) {
-              tma_load_2d_hint(sB_lo(stage), mb_lo, &full[stage], kc,
+              tma_load_2d_hint(sB_hi(stage), mb_hi, &full[stage], kc,
                                (int)col0, pol);
-              tma_load_2d_hint(sB_lo(stage) + kTileA, mb_lo, &full[stage],
+              tma_load_2d_hint(sB_hi(stage) + kTileA, mb_hi, &full[stage],
                                kc, (int)col0 + kBM, pol);
             } else {
-              tma_load_2d_mc(sB_lo(stage) + crank * kTileA, mb_lo,
+              // both CTAs need all 256 B rows: each loads its 128 and
+              // multicasts them to the pair
+              tma_load_2d_mc(sB_hi(stage) + crank * kTileA, mb_hi,
                              &full[stage], kc, (int)(col0 + crank * kBM), 3,
                              pol);
+            }
+            if (NPROD > 1) {
+              tma_load_2d_hint(sA_lo(stage), &tm_lo, &full[stage], kc,
+                               (int)row0, pol);
+              if constexpr (CL == 1) {
+                tma_load_2d_hint(sB_lo(stage), mb_lo, &full[stage], kc,
+                                 (int)col0, pol);
+                tma_load_2d_hint(sB_lo(stage) + kTileA, mb_lo, &full[stage],
+                                 kc, (int)col0 + kBM, pol);
+              } else {
+                tma_load_2d_mc(sB_lo(stage) + crank * kTileA, mb_lo,
+                               &full[stage], kc, (int)(col0 + crank * kBM), 3,
+                               pol);
+              }
             }
           }
           issued_mask |= 1u << stage;

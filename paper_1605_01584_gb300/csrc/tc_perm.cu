@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
     for (int g = 0; g < NG; ++g) {
       const int64_t v = lane + 32 * g;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) idx[8 * g + t] = v < ngroups ? pi[v * 8 + t] : -1;
+      for (int t = 0; t < 8; ++t)
+        idx[8 * g + t] = v < ngroups ? pi[v * 8 + t] : -1;
     }
   }
   // RR rows per warp and iteration (rows j, j + W, ...), staged together so
@@ -453,37 +454,31 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 tma_load_3d_pair(sB_hi(stage), &tp_hi, fb, kc, (int)col0, kk);
                 tma_load_3d_pair(sB_lo(stage), &tp_lo, fb, kc, (int)col0, kk);
               }
-              issued_mask |= 1u << stage;
-              last_phase[stage] = phase;
-              if (++stage == S) {
-                stage = 0;
-                phase ^= 1u;
-              }
-              continue;
-            }
-            mbar_arrive_expect_tx(&full[stage], bytes);
-            if (!RESA) {
-              tma_load_2d_hint(sA_hi(stage, kb), &tz_hi, &full[stage], kc,
-                               (int)row0, pol);
-              tma_load_2d_hint(sA_lo(stage, kb), &tz_lo, &full[stage], kc,
-                               (int)row0, pol);
-            }
-            if (pass < 0) {
-              tma_load_2d_hint(sB_hi(stage), &tz_hi, &full[stage], kc,
-                               (int)col0, pol);
-              tma_load_2d_hint(sB_lo(stage), &tz_lo, &full[stage], kc,
-                               (int)col0, pol);
             } else {
-              const int ka = k0 + 2 * pass;
-              tma_load_3d(sB_hi(stage), &tp_hi, &full[stage], kc, (int)col0,
-                          ka);
-              tma_load_3d(sB_lo(stage), &tp_lo, &full[stage], kc, (int)col0,
-                          ka);
-              if (two) {
-                tma_load_3d(sB_hi(stage) + kPTile, &tp_hi, &full[stage], kc,
-                            (int)col0, ka + 1);
-                tma_load_3d(sB_lo(stage) + kPTile, &tp_lo, &full[stage], kc,
-                            (int)col0, ka + 1);
+              mbar_arrive_expect_tx(&full[stage], bytes);
+              if (!RESA) {
+                tma_load_2d_hint(sA_hi(stage, kb), &tz_hi, &full[stage], kc,
+                                 (int)row0, pol);
+                tma_load_2d_hint(sA_lo(stage, kb), &tz_lo, &full[stage], kc,
+                                 (int)row0, pol);
+              }
+              if (pass < 0) {
+                tma_load_2d_hint(sB_hi(stage), &tz_hi, &full[stage], kc,
+                                 (int)col0, pol);
+                tma_load_2d_hint(sB_lo(stage), &tz_lo, &full[stage], kc,
+                                 (int)col0, pol);
+              } else {
+                const int ka = k0 + 2 * pass;
+                tma_load_3d(sB_hi(stage), &tp_hi, &full[stage], kc, (int)col0,
+                            ka);
+                tma_load_3d(sB_lo(stage), &tp_lo, &full[stage], kc, (int)col0,
+                            ka);
+                if (two) {
+                  tma_load_3d(sB_hi(stage) + kPTile, &tp_hi, &full[stage], kc,
+                              (int)col0, ka + 1);
+                  tma_load_3d(sB_lo(stage) + kPTile, &tp_lo, &full[stage], kc,
+                              (int)col0, ka + 1);
+                }
               }
             }
             issued_mask |= 1u << stage;
