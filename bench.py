@@ -564,7 +564,12 @@ def run_perm(args):
            "roofline_split_executed": {
                "bound": "tensor", "achieved": exec_flops / (ms / 1e3) / 1e12,
                "peak": bf16_sus, "unit": "TFLOP/s",
-               "frac": exec_flops / (ms / 1e3) / 1e12 / bf16_sus}}
+               "frac": exec_flops / (ms / 1e3) / 1e12 / bf16_sus,
+               "note": "3-product split work of the P permutations and one "
+                       "r_obs pass per 128 x 128 tile; the kernel also "
+                       "repeats r_obs per chunk of permutations and pads "
+                       "lone tiles in the pair form (about 5% more tensor "
+                       "work, not counted)"}}
     print(json.dumps(out), flush=True)
     return 0
 
