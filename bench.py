@@ -581,7 +581,8 @@ def run_batched(args):
     import paper_1605_01584_gb300 as pcc
     import synth
     pcc.load()
-    shapes = synth.uneven_shapes()
+    # the first `--matrices` of the 64 (a smaller case for profiling)
+    shapes = synth.uneven_shapes()[:max(1, args.matrices)]
     Xs, Zs, Rs = [], [], []
     t0 = time.time()
     for b, (n, l) in enumerate(shapes):
@@ -626,8 +627,8 @@ def run_batched(args):
            (ms / 1e3), "unit": "Gpair*samples/s", "ms_per_step": ms,
            "ms_per_step_stream": ms_stream, "graph": ms_graph is not None,
            "ms_batched_kernel": ms_k, "status": st,
-           "config": {"workload": "64 uneven matrices n~U{500..20000}, "
-                      "l~U{32..2048}", "split": args.prec,
+           "config": {"workload": f"{len(shapes)} uneven matrices "
+                      "n~U{500..20000}, l~U{32..2048}", "split": args.prec,
                       "matrices": len(shapes), "gen_seconds": gen_s},
            "roofline": {"bound": "hbm", "achieved": out_bytes / (ms_k / 1e3)
                         / 1e9, "peak": hbm, "unit": "GB/s",
@@ -778,6 +779,8 @@ def main():
                     choices=["allpairs", "perm", "batched", "cross",
                              "paper"])
     ap.add_argument("--n", type=int, default=N_GENES)
+    ap.add_argument("--matrices", type=int, default=64,
+                    help="matrices of the batched workload (its first K)")
     ap.add_argument("--P", type=int, default=1000,
                     help="permutations of the perm workload")
     ap.add_argument("--l", type=int, default=L_SAMPLES)
