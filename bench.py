@@ -585,8 +585,9 @@ def run_batched(args):
     shapes = synth.uneven_shapes()[:max(1, args.matrices)]
     Xs, Zs, Rs = [], [], []
     t0 = time.time()
-    for b, (n, l) in enumerate(shapes):
-        X = synth.counts_log(n, l, 5 * 1000 + b)
+    gen = synth.counts_log_many(shapes, [5 * 1000 + b
+                                         for b in range(len(shapes))])
+    for X, (n, l) in zip(gen, shapes):
         Xd = torch.from_numpy(X).cuda()
         Xs.append(Xd)
         Zs.append(pcc.pcc_standardize(Xd, args.prec))

@@ -17,6 +17,8 @@ Workloads (stand-ins for the paper's data, Section IV):
   * ``fisher_yates_perms`` -- P seeded sample permutations (splitmix64 +
     Lemire's unbiased bounded draw), one row per permutation.
   * ``uneven_shapes``   -- the (n_b, l_b) list of a batch of uneven matrices.
+  * ``counts_log_many`` -- many ``counts_log`` matrices drawn in parallel
+    (spawned processes), identical to the serial calls.
 """
 from __future__ import annotations
 
@@ -28,6 +30,7 @@ __all__ = [
     "uniform01",
     "fisher_yates_perms",
     "uneven_shapes",
+    "counts_log_many",
     "module_assignment",
     "splitmix64",
 ]
@@ -95,6 +98,31 @@ def counts_log(n: int, l: int, seed: int, n_modules: int = 200,
         x[sel] += a[sel, None] * f[mod[sel]]
     x = np.ascontiguousarray(x.astype(dtype))
     return (x, mod) if return_modules else x
+
+
+def _counts_log_job(job):
+    n, l, seed, return_modules = job
+    return counts_log(n, l, seed, return_modules=return_modules)
+
+
+def counts_log_many(shapes, seeds, return_modules: bool = False,
+                    workers: int | None = None):
+    """``counts_log(n, l, seed)`` for every (n, l) of ``shapes`` with the
+    matching seed, drawn in a pool of spawned processes (each matrix has its
+    own generator, so the arrays equal the serial calls').  Spawned, not
+    forked, so that it is safe after CUDA has been initialised."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    jobs = [(int(n), int(l), int(s), return_modules)
+            for (n, l), s in zip(shapes, seeds)]
+    if workers is None:
+        workers = min(len(jobs), os.cpu_count() or 1, 16)
+    if workers <= 1 or len(jobs) <= 1:
+        return [_counts_log_job(j) for j in jobs]
+    with cf.ProcessPoolExecutor(workers,
+                                mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_counts_log_job, jobs))
 
 
 def uniform01(n: int, l: int, seed: int, dtype=np.float32) -> np.ndarray:

@@ -1,6 +1,8 @@
 """GPU parity of the batched uneven launch (pcc_allpairs_upper_batched):
 each matrix against its own single-matrix run and against the oracle, plus
 CUDA-graph replay of the launch."""
+import json
+
 import numpy as np
 import pytest
 
@@ -86,33 +88,46 @@ def test_batched_plan_reuse_and_graph_replay(pcc_gpu):
 
 
 def test_batched_uneven_workload_sampled(pcc_gpu):
-    """The first 12 matrices of the 64-matrix uneven workload (n ~
-    U{500..20000}, l ~ U{32..2048}), 20,000 sampled pairs each."""
+    """The whole 64-matrix uneven workload (n ~ U{500..20000}, l ~
+    U{32..2048}) in the launches the benchmark times: one batched
+    standardize, one batched pair launch.  Per matrix, 10^5 uniformly
+    sampled pairs plus every pair of its first 5 planted modules (where
+    |r| -> 1 and the split error peaks) against the oracle."""
     torch = _torch()
     pcc = pcc_gpu
-    shapes = synth.uneven_shapes()[:12]
-    Xs, Zs, Rs = [], [], []
-    for b, (n, l) in enumerate(shapes):
-        X = synth.counts_log(n, l, 5 * 1000 + b)
-        Xs.append(X)
-        Zs.append(pcc.pcc_standardize(torch.from_numpy(X).cuda(), "auto"))
-        Rs.append(torch.empty(n * (n - 1) // 2, device="cuda"))
+    shapes = synth.uneven_shapes()
+    gen = synth.counts_log_many(shapes, [5 * 1000 + b
+                                         for b in range(len(shapes))],
+                                return_modules=True)
+    Xs = [torch.from_numpy(X).cuda() for X, _ in gen]
+    Zs = pcc.pcc_standardize_batched(Xs, "auto")
+    Rs = [torch.empty(n * (n - 1) // 2, device="cuda") for n, _ in shapes]
     pcc.pcc_allpairs_upper_batched(Zs, Rs)
     assert pcc.pcc_sync_status(Zs[0]) == 0
     rng = np.random.default_rng(105)
-    worst = 0.0
-    for b, (n, l) in enumerate(shapes):
-        I = rng.integers(0, n, 20000)
-        J = rng.integers(0, n, 20000)
+    worst, checked = 0.0, 0
+    for b, ((n, l), (X, mod)) in enumerate(zip(shapes, gen)):
+        I = rng.integers(0, n, 100_000)
+        J = rng.integers(0, n, 100_000)
         keep = I != J
-        I, J = np.minimum(I, J)[keep], np.maximum(I, J)[keep]
+        I, J = [np.minimum(I, J)[keep]], [np.maximum(I, J)[keep]]
+        for m in range(min(int(mod.max()) + 1, 5)):
+            g = np.nonzero(mod == m)[0]
+            u, v = np.triu_indices(len(g), 1)
+            I.append(g[u])
+            J.append(g[v])
+        I, J = np.concatenate(I), np.concatenate(J)
         idx = torch.from_numpy(I * (2 * n - I - 1) // 2 + (J - I - 1)).cuda()
         got = Rs[b][idx].cpu().numpy().astype(np.float64)
-        want = oracle.pcc_pairs(Xs[b], I, J)
-        assert np.array_equal(np.isnan(got), np.isnan(want))
+        want = oracle.pcc_pairs(X, I, J)
+        assert np.array_equal(np.isnan(got), np.isnan(want)), b
         ok = ~np.isnan(want)
-        worst = max(worst, float(np.max(np.abs(got[ok] - want[ok]))))
-    assert worst <= 1e-5, worst
+        err = float(np.max(np.abs(got[ok] - want[ok])))
+        assert err <= 1e-5, (b, n, l, err)
+        worst = max(worst, err)
+        checked += int(ok.sum())
+    print(json.dumps({"batched_workload_max_abs_dr": worst,
+                      "pairs_checked": checked}))
 
 
 def test_batched_invalid_arguments(pcc_gpu):

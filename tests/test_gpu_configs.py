@@ -9,7 +9,10 @@ on outputs the oracle can compute one by one.
   output-bound        n=65536 x l=512: the fused packed + edge pass; max|dr|
                       on 10^6 sampled pairs plus module pairs, and the edge
                       list of 48 sampled row panels equal to the oracle's
-                      outside the +-1e-5 band around tau = 0.8.
+                      outside the +-1e-5 band around tau = 0.8; over the
+                      whole triangle, the edge list equal to the stored
+                      |R| >= tau bit for bit, and every pair whose stored r
+                      is within 1e-4 of tau against the oracle.
 The measured errors are written to tests' stdout (pytest -s) as JSON.
 """
 import json
@@ -28,19 +31,25 @@ def _torch():
     return torch
 
 
-def _sample_pairs(n, k, seed, mod):
-    rng = np.random.default_rng(seed)
-    J = rng.integers(0, n * (n - 1) // 2, k)
-    # inverse of the packed numbering (row = largest i with base <= J)
+def _coords(n, J):
+    """(i, j) of packed strict-upper indices J (row = largest i whose first
+    index is <= J), with an integer fix-up after the FP64 root."""
+    J = np.asarray(J, dtype=np.int64)
     i = np.floor((2 * n - 1 - np.sqrt((2 * n - 1) ** 2 - 8 * J)) / 2)
     i = i.astype(np.int64)
     start = i * (2 * n - i - 1) // 2
     i = np.where(start > J, i - 1, i)
-    start = i * (2 * n - i - 1) // 2
     nxt = (i + 1) * (2 * n - i - 2) // 2
     i = np.where(nxt <= J, i + 1, i)
     start = i * (2 * n - i - 1) // 2
     j = J - start + i + 1
+    assert np.all(start <= J) and np.all(i < j) and np.all(j < n)
+    return i, j
+
+
+def _sample_pairs(n, k, seed, mod):
+    rng = np.random.default_rng(seed)
+    i, j = _coords(n, rng.integers(0, n * (n - 1) // 2, k))
     I, Jc = [i], [j]
     for m in range(min(mod.max() + 1, 40)):
         g = np.nonzero(mod == m)[0]
@@ -57,6 +66,16 @@ def _gather(R, n, I, J):
     torch = _torch()
     idx = torch.from_numpy(I * (2 * n - I - 1) // 2 + (J - I - 1)).cuda()
     return R[idx].cpu().numpy().astype(np.float64)
+
+
+def _where_abs_ge(R, t, chunk=1 << 28):
+    """Sorted indices of R with |R| >= t, scanned in chunks."""
+    torch = _torch()
+    out = []
+    for c0 in range(0, R.numel(), chunk):
+        idx = torch.nonzero(R[c0:c0 + chunk].abs() >= t).squeeze(1)
+        out.append(idx.cpu().numpy().astype(np.int64) + c0)
+    return np.concatenate(out)
 
 
 def test_precision_workload_every_form(pcc_gpu):
@@ -122,8 +141,33 @@ def test_output_bound_workload_fused(pcc_gpu):
             band_extra += (a, b) in got_e
             band_missing += (a, b) in want_e
         checked += len(want_e)
-    print(json.dumps({"output_bound_max_abs_dr": err, "edges_total": c,
-                      "edges_checked": checked, "band_extra": band_extra,
-                      "band_missing": band_missing}))
     assert err <= 1e-5
     assert c < cap
+    # The whole triangle.  The edge r and the stored R come from the same
+    # FP32 value, so the edge list must be exactly the pairs whose stored
+    # |r| >= tau, each once, with r equal to R bit for bit.
+    Jq = ei * (2 * n - ei - 1) // 2 + (ej - ei - 1)
+    assert np.all(ei < ej) and np.all(ej < n)
+    assert np.unique(Jq).size == c
+    assert np.array_equal(
+        R[torch.from_numpy(Jq).cuda()].cpu().numpy().view(np.uint32),
+        er.view(np.uint32))
+    above = _where_abs_ge(R, tau)  # NaN (flagged rows) compares false
+    assert np.array_equal(above, np.sort(Jq))
+    # every pair of the triangle whose stored r lies within 1e-4 of the
+    # threshold, against the oracle: a pair outside this set that the oracle
+    # puts past tau + 1e-5 would need an error of 9e-5
+    near = _where_abs_ge(R, tau - 1e-4)
+    ni, nj = _coords(n, near)
+    want_n = oracle.pcc_pairs(X, ni, nj)
+    got_n = R[torch.from_numpy(near).cuda()].cpu().numpy().astype(np.float64)
+    err_near = float(np.max(np.abs(got_n - want_n)))
+    assert err_near <= 1e-5
+    is_edge = np.abs(got_n) >= tau
+    assert not np.any(is_edge & (np.abs(want_n) < tau - 1e-5))
+    assert not np.any(~is_edge & (np.abs(want_n) >= tau + 1e-5))
+    print(json.dumps({"output_bound_max_abs_dr": err, "edges_total": c,
+                      "edges_checked": checked, "band_extra": band_extra,
+                      "band_missing": band_missing,
+                      "near_tau_pairs": int(near.size),
+                      "near_tau_max_abs_dr": err_near}))

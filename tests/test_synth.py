@@ -32,3 +32,17 @@ def test_uneven_shapes_ranges():
     s = synth.uneven_shapes()
     assert len(s) == 64
     assert all(500 <= n <= 20000 and 32 <= l <= 2048 for n, l in s)
+
+
+def test_counts_log_many_equals_serial_calls():
+    shapes = [(90, 17), (200, 33), (81, 64)]
+    seeds = [7, 8, 9]
+    got = synth.counts_log_many(shapes, seeds, return_modules=True,
+                                workers=2)
+    for (n, l), s, (X, mod) in zip(shapes, seeds, got):
+        X0, mod0 = synth.counts_log(n, l, s, return_modules=True)
+        assert X.dtype == X0.dtype and X.shape == (n, l)
+        assert np.array_equal(X.view(np.uint32), X0.view(np.uint32))
+        assert np.array_equal(mod, mod0)
+    assert [x.shape for x in synth.counts_log_many(shapes[:1], [7])] == \
+        [(90, 17)]
