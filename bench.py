@@ -265,6 +265,19 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def max_over_ranks(x: float, dist=None) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself
+    without a process group.  The reduction runs on the GPU under NCCL and
+    on the host under gloo."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args):
     import torch
     import paper_1605_01584_gb300 as pcc
@@ -338,11 +351,7 @@ def run_gpu(args):
     if st != 0:
         raise RuntimeError(f"device status {pcc.pcc_status_string(st)}")
 
-    ms_step = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(total_ms / args.steps, dist)
     value = gpair_samples(n, l) * world / (ms_step / 1e3)
 
     # roofline of the dominant kernel (the fused pair kernel)
@@ -456,6 +465,8 @@ def run_gpu(args):
 
         e2e_step()
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         ne = 0
         # each step ends with its results on the host; the host link's rate
         # varies from step to step (shared with other work on the machine),
@@ -465,7 +476,7 @@ def run_gpu(args):
             t0 = time.perf_counter()
             ne = e2e_step()
             walls.append((time.perf_counter() - t0) * 1e3)
-        e2e_ms = statistics.median(walls)
+        e2e_ms = max_over_ranks(statistics.median(walls), dist)
         out["e2e"] = {"value": gpair_samples(n, l) * world / (e2e_ms / 1e3),
                       "unit": UNIT, "ms_per_step": e2e_ms,
                       "ms_per_step_mean": statistics.fmean(walls),
@@ -474,7 +485,7 @@ def run_gpu(args):
                       "mode": args.e2e_mode,
                       "d2h_bytes_per_step": npairs * 4 + 8 + ne * 12}
 
-    if rank == 0 and not args.skip_cpu:
+    if rank == 0 and world == 1 and not args.skip_cpu:
         v, cores, sample = oracle_rate(X, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores,
                                "kind": "oracle", "sample": sample,

@@ -145,22 +145,27 @@ def test_invalid_ranges(pcc_gpu):
 
 def test_perm_full_config_sampled(pcc_gpu):
     """The batched permutation workload: n=4096 x l=256, P=1000 seeded
-    Fisher-Yates permutations, checked on sampled pairs plus planted-module
-    pairs against the oracle under the band rule."""
+    Fisher-Yates permutations.  10^5 uniformly sampled pairs plus every pair
+    of every planted module against the oracle under the band rule; over
+    the whole triangle, 0 <= count <= P (flagged rows are covered by the
+    ragged-shape cases: this workload has no constant row)."""
     n, l, P = 4096, 256, 1000
     X, mod = synth.counts_log(n, l, seed=4, return_modules=True)
     perms = synth.fisher_yates_perms(P, l, seed=4)
     got, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
     assert st == 0
+    assert got.min() >= 0 and got.max() <= P
     rng = np.random.default_rng(104)
-    I = rng.integers(0, n, 1500)
-    J = rng.integers(0, n, 1500)
+    I = rng.integers(0, n, 100_000)
+    J = rng.integers(0, n, 100_000)
     keep = I != J
-    I, J = np.minimum(I, J)[keep], np.maximum(I, J)[keep]
-    m0 = np.nonzero(mod == 0)[0]
-    mi, mj = np.triu_indices(len(m0), 1)
-    I = np.concatenate([I, m0[mi]])
-    J = np.concatenate([J, m0[mj]])
+    I, J = [np.minimum(I, J)[keep]], [np.maximum(I, J)[keep]]
+    for m in range(int(mod.max()) + 1):
+        g = np.nonzero(mod == m)[0]
+        mi, mj = np.triu_indices(len(g), 1)
+        I.append(g[mi])
+        J.append(g[mj])
+    I, J = np.concatenate(I), np.concatenate(J)
     exact, tot = check_band(X, perms, got, I, J)
     assert exact > 0.5 * tot
 

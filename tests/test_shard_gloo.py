@@ -104,3 +104,40 @@ def test_two_rank_gloo_union_is_the_triangle():
     assert np.array_equal(np.isnan(got), np.isnan(want))
     ok = ~np.isnan(want)
     assert np.array_equal(got[ok], want[ok])
+
+
+def _bench_rank_main(rank, world, port, out_q):
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # each rank's step time differs; every rank must see the slowest
+        got = bench.max_over_ranks(4.5 + 1.25 * rank, dist)
+        dist.barrier()
+        out_q.put((rank, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_times_are_the_max_over_ranks():
+    """bench.py's multi-rank timing: the step time every rank reports is
+    the slowest rank's (the whole-job value divides all ranks' work by it)."""
+    import multiprocessing as mp
+
+    import bench
+    assert bench.max_over_ranks(3.25) == 3.25
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_rank_main, args=(r, 2, port, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=300) for _ in range(2))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert res == {0: 5.75, 1: 5.75}
