@@ -94,6 +94,22 @@ def test_fp64_modules_config(pcc_gpu):
     compare(got, want, 1e-12, "fp64 2000x128")
 
 
+@pytest.mark.parametrize("n,l,prec", [
+    (300, 1500, "fp16x3s"),   # two accumulators (l > 1,024)
+    (300, 1500, "bf16x3"),
+    (257, 2049, "auto"),      # AUTO switches to BF16X3 above 2,048
+    (300, 5000, "auto"),      # the paper's row length
+])
+def test_long_rows_parity(pcc_gpu, n, l, prec):
+    """Rows past 1,024 samples (the K blocks split over two TMEM
+    accumulators, folded before the stores) against the oracle, with
+    planted modules (r -> 1), a constant row and a 1e5 offset row."""
+    X = _data(n, l, seed=3000 + n + l)
+    got, _ = gpu_allpairs(pcc_gpu, X, prec)
+    want = oracle.pcc_upper(X)
+    compare(got, want, 1e-5, f"{prec} n={n} l={l}")
+
+
 @pytest.mark.parametrize("prec", ["bf16x3", "fp16x3s"])
 def test_perfect_correlation_rows(pcc_gpu, prec):
     """|r| -> 1 is where the dropped lo*lo term peaks: rows that are exact
