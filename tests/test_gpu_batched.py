@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import synth
+from gpu_compare import max_abs_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -126,8 +127,23 @@ def test_batched_uneven_workload_sampled(pcc_gpu):
         assert err <= 1e-5, (b, n, l, err)
         worst = max(worst, err)
         checked += int(ok.sum())
+    # every pair of every matrix against its FP64 CUDA-core triangle
+    worst_all = 0.0
+    for b, (n, l) in enumerate(shapes):
+        Z64 = pcc.pcc_standardize(Xs[b], "fp64")
+        R64 = torch.empty(n * (n - 1) // 2, dtype=torch.float64,
+                          device="cuda")
+        pcc.pcc_allpairs_upper(Z64, R64)
+        assert pcc.pcc_sync_status(Z64) == 0
+        e, nan_differs = max_abs_diff(Rs[b], R64)
+        assert not nan_differs, b
+        assert e <= 1e-5, (b, n, l, e)
+        worst_all = max(worst_all, e)
+        Z64.close()
+        del R64
     print(json.dumps({"batched_workload_max_abs_dr": worst,
-                      "pairs_checked": checked}))
+                      "pairs_checked": checked,
+                      "all_pairs_max_abs_dr_vs_fp64_path": worst_all}))
 
 
 def test_batched_invalid_arguments(pcc_gpu):

@@ -4,7 +4,8 @@ on outputs the oracle can compute one by one.
   precision workload  n=16384 x l=1024: max|dr| of every stored form on
                       10^6 uniformly sampled pairs plus every pair of the
                       planted modules (where |r| -> 1 and the split error
-                      peaks); split forms and FP32 must be <= 1e-5, the
+                      peaks), and on every pair against the FP64 CUDA-core
+                      triangle; split forms and FP32 must be <= 1e-5, the
                       single-BF16 form is reported only.
   output-bound        n=65536 x l=512: the fused packed + edge pass; max|dr|
                       on 10^6 sampled pairs plus module pairs, and the edge
@@ -24,6 +25,7 @@ import pytest
 
 import oracle
 import synth
+from gpu_compare import max_abs_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -76,21 +78,6 @@ def _gather64(R, n, I, J):
     return R[idx].cpu().numpy()
 
 
-def _max_abs_diff(a, b, chunk=1 << 28):
-    """max |a - b| over entries where neither is NaN, in FP64, and whether
-    the NaN patterns differ; scanned in chunks."""
-    torch = _torch()
-    worst, differs = 0.0, False
-    for c0 in range(0, a.numel(), chunk):
-        x = a[c0:c0 + chunk].double()
-        y = b[c0:c0 + chunk]
-        nx, ny = torch.isnan(x), torch.isnan(y)
-        differs |= bool((nx != ny).any().item())
-        d = torch.where(nx | ny, torch.zeros_like(x), (x - y).abs())
-        worst = max(worst, float(d.max().item()))
-    return worst, differs
-
-
 def _where_abs_ge(R, t, chunk=1 << 28):
     """Sorted indices of R with |R| >= t, scanned in chunks."""
     torch = _torch()
@@ -111,7 +98,15 @@ def test_precision_workload_every_form(pcc_gpu):
     ok = ~np.isnan(want)
     Xd = torch.from_numpy(X).cuda()
     R = torch.empty(n * (n - 1) // 2, device="cuda")
-    report = {}
+    # the FP64 CUDA-core triangle, checked against the oracle on the
+    # sampled pairs, is the reference for every pair
+    Z64 = pcc.pcc_standardize(Xd, "fp64")
+    R64 = torch.empty(n * (n - 1) // 2, dtype=torch.float64, device="cuda")
+    pcc.pcc_allpairs_upper(Z64, R64)
+    assert pcc.pcc_sync_status(Z64) == 0
+    err64 = float(np.max(np.abs(_gather64(R64, n, I, J)[ok] - want[ok])))
+    assert err64 <= 1e-12
+    report, report_all = {}, {}
     for prec in ("bf16x3", "fp16x3s", "bf16x1", "fp32", "auto"):
         Z = pcc.pcc_standardize(Xd, prec)
         pcc.pcc_allpairs_upper(Z, R)
@@ -119,11 +114,16 @@ def test_precision_workload_every_form(pcc_gpu):
         got = _gather(R, n, I, J)
         assert np.array_equal(np.isnan(got), np.isnan(want)), prec
         report[prec] = float(np.max(np.abs(got[ok] - want[ok])))
+        report_all[prec], nan_differs = max_abs_diff(R, R64)
+        assert not nan_differs, prec
         Z.close()
     print(json.dumps({"precision_workload_max_abs_dr": report,
-                      "pairs_checked": int(ok.sum())}))
+                      "pairs_checked": int(ok.sum()),
+                      "fp64_path_vs_oracle": err64,
+                      "all_pairs_max_abs_dr_vs_fp64_path": report_all}))
     for prec in ("bf16x3", "fp16x3s", "fp32", "auto"):
         assert report[prec] <= 1e-5, (prec, report[prec])
+        assert report_all[prec] <= 1e-5, (prec, report_all[prec])
     assert report["bf16x1"] <= 2e-2
 
 
@@ -199,7 +199,7 @@ def test_output_bound_workload_fused(pcc_gpu):
     assert pcc.pcc_sync_status(Z64) == 0
     err64 = float(np.max(np.abs(_gather64(R64, n, I, J)[ok] - want[ok])))
     assert err64 <= 1e-12
-    err_all, nan_differs = _max_abs_diff(R, R64)
+    err_all, nan_differs = max_abs_diff(R, R64)
     assert not nan_differs
     assert err_all <= 1e-5
     print(json.dumps({"output_bound_max_abs_dr": err, "edges_total": c,
