@@ -202,3 +202,48 @@ def test_cross_invalid_arguments(pcc_gpu):
         pcc.pcc_cross_allpairs(ZX, ZY2, R, 100, 0, T + 1)
     pcc.pcc_cross_allpairs(ZX, ZY2, R, 100)
     assert pcc.pcc_sync_status(ZX) == 0
+
+
+def test_cross_full_workload(pcc_gpu):
+    """The cross workload at its benchmarked size: X 65,536 x 512 against
+    Y 32,768 x 512 (log counts, seeds 6 and 7), dense FP32 R of 8.6 GB, in
+    the default form.  10^6 sampled (i, j) against the oracle, and every
+    pair against the FP64 CUDA-core cross matrix (itself within 1e-12 of
+    the oracle on the samples)."""
+    import json
+
+    import torch
+
+    from gpu_compare import max_abs_diff
+    pcc = pcc_gpu
+    nx, ny, l = 65536, 32768, 512
+    X = synth.counts_log(nx, l, 6)
+    Y = synth.counts_log(ny, l, 7)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    ZX, ZY = pcc.pcc_standardize(Xd, "auto"), pcc.pcc_standardize(Yd, "auto")
+    R = torch.empty((nx, ny), dtype=torch.float32, device="cuda")
+    pcc.pcc_cross_allpairs(ZX, ZY, R)
+    assert pcc.pcc_sync_status(ZX) == 0
+    rng = np.random.default_rng(106)
+    I = rng.integers(0, nx, 1_000_000)
+    J = rng.integers(0, ny, 1_000_000)
+    want = oracle.cross_pairs(X, Y, I, J)
+    ok = ~np.isnan(want)
+    idx = torch.from_numpy(I * ny + J).cuda()
+    got = R.view(-1)[idx].cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    err = float(np.max(np.abs(got[ok] - want[ok])))
+    assert err <= 1e-5
+    X64, Y64 = pcc.pcc_standardize(Xd, "fp64"), pcc.pcc_standardize(Yd, "fp64")
+    R64 = torch.empty((nx, ny), dtype=torch.float64, device="cuda")
+    pcc.pcc_cross_allpairs(X64, Y64, R64)
+    assert pcc.pcc_sync_status(X64) == 0
+    err64 = float(np.max(np.abs(R64.view(-1)[idx].cpu().numpy()[ok] -
+                                want[ok])))
+    assert err64 <= 1e-12
+    err_all, nan_differs = max_abs_diff(R.view(-1), R64.view(-1))
+    assert not nan_differs
+    assert err_all <= 1e-5
+    print(json.dumps({"cross_workload_max_abs_dr": err,
+                      "fp64_path_vs_oracle": err64,
+                      "all_pairs_max_abs_dr_vs_fp64_path": err_all}))
