@@ -134,11 +134,17 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the pair kernel's sources with comments and blank space
+    removed, so that an edit of a comment keeps the committed counters."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("tc_pairs.cu", "tc_epilogue.cuh", "pcc_ptx.cuh", "pcc_sched.h"):
-        h.update(open(os.path.join(ROOT, "paper_1605_01584_gb300", "csrc",
-                                   f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1605_01584_gb300", "csrc", f),
+                   encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -30,7 +30,11 @@
 //               contiguous), clamp to [-1,1], NaN for flagged rows, and the
 //               optional warp-aggregated edge append.
 // The two accumulators let the epilogue of one unit overlap the MMAs of the
-// next.
+// next.  Rows longer than 1,024 samples (kalt) split a unit's K blocks in
+// two halves, one per accumulator: the FP32 accumulation rounds its running
+// sum toward zero, and halving each sum's length halves that bias.  The
+// epilogue adds the first accumulator into the second in TMEM (fold_acc),
+// releases the first to the next unit at once, and stores from the second.
 //
 // CROSS: the non-symmetric job matrix between the rows of two matrices
 // (Section III-B, Eq. (7)-(8)): A rows come from the first, B rows from the
