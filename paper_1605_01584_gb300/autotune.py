@@ -24,6 +24,7 @@ from __future__ import annotations
 import itertools
 import json
 import math
+import numbers
 import os
 import statistics
 
@@ -72,17 +73,26 @@ def save_cache(cache: dict, path: str | None = None) -> None:
     os.replace(tmp, path)
 
 
+def _usable(entry) -> bool:
+    """An entry written by tune_pairs: a 'best' record with every knob that
+    apply() sets (a truncated or hand-edited cache is skipped, not fatal)."""
+    if not isinstance(entry, dict) or not isinstance(entry.get("best"), dict):
+        return False
+    return all(isinstance(entry["best"].get(k), numbers.Integral)
+               for k in ("stage_k", "cluster", "band_rows"))
+
+
 def lookup(n: int, l: int, prec: str, cache: dict | None = None):
     """Best known knobs for (n, l, prec): the exact bucket, else the entry
     with the same split and padded l whose n is closest (log scale)."""
     cache = load_cache() if cache is None else cache
     key = bucket(n, l, prec)
-    if key in cache:
+    if _usable(cache.get(key)):
         return cache[key]["best"]
     lp = (l + 63) // 64 * 64
     best, dist = None, None
     for k, v in cache.items():
-        if not k.endswith(f"_l{lp}_{prec}") or "best" not in v:
+        if not k.endswith(f"_l{lp}_{prec}") or not _usable(v):
             continue
         nb = int(k.split("_")[0][1:])
         d = abs(math.log2(nb) - math.log2(max(n, 2)))

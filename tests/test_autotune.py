@@ -51,3 +51,18 @@ def test_tune_small_shape_and_apply(pcc_gpu, tmp_path):
     finally:
         pcc.pcc_set_tuning(before["stage_k"], before["cluster"],
                            before["band_rows"], pair_mma=before["pair_mma"])
+
+
+def test_lookup_skips_unusable_entries():
+    good = {"best": {"stage_k": 32, "cluster": 2, "band_rows": 32}}
+    cache = {
+        "n65536_l512_bf16x3": {"runs": []},                 # no 'best'
+        "n32768_l512_bf16x3": {"best": {"stage_k": 64}},    # knobs missing
+        "n16384_l512_bf16x3": good,
+        "n8192_l512_bf16x3": "garbage",
+    }
+    # the exact bucket and the nearer entry are unusable: the usable one
+    # further away is taken
+    assert autotune.lookup(65536, 512, "bf16x3", cache) == good["best"]
+    assert autotune.lookup(65536, 512, "fp16x3s", cache) is None
+    assert autotune.lookup(65536, 512, "bf16x3", {}) is None
