@@ -70,10 +70,11 @@ typedef enum {
     PCC_PREC_BF16X1 = 5,  /* Z = bf16(z), one product (reported only:
                              about 1e-3 error) */
     PCC_PREC_AUTO = 6     /* the split form with the smaller worst-case
-                             error for the row length: FP16X3S for
-                             l <= 2048, else BF16X3 (beyond l = 2048 no
-                             split form stays within 1e-5 on every input;
-                             PCC_PREC_FP32 does) */
+                             error: FP16X3S at every l (on rows whose mass
+                             sits in one sample BF16X3's BF16 halves alone
+                             reach 1.0-1.3e-5; FP16X3S stays within 1e-5,
+                             with long rows accumulated in chunks of at
+                             most 640 samples) */
 } pcc_prec;
 
 typedef struct pcc_zmat pcc_zmat; /* opaque, library-owned */
@@ -104,6 +105,21 @@ typedef struct {
 pcc_status pcc_standardize(const void *X, pcc_dtype xt, int64_t n, int64_t l,
                            int64_t ldx, pcc_prec prec, pcc_zmat **Z,
                            void *stream);
+
+/* pcc_standardize from a HOST matrix (Eq. (5), Algorithm 3, as above):
+ * the call copies X_host (host memory, n x l, leading dimension ldx >= l,
+ * element type xt) into a device copy owned by *Z, then standardizes it on
+ * `stream`.  With pinned (page-locked) X_host the copy is asynchronous and
+ * X_host must stay unchanged until the stream reaches it; with pageable
+ * memory the copy completes before the call returns.  The device copy is
+ * allocated by the first call that needs it (or a larger one) and reused
+ * after, so later calls of the same size allocate nothing.  This is the
+ * entry of a program whose data start in host memory (the paper's offload
+ * model, Section III-C: input sent once, results streamed back).
+ * Errors: as pcc_standardize, PCC_ERR_INVALID_ARG for a NULL X_host. */
+pcc_status pcc_standardize_host(const void *X_host, pcc_dtype xt, int64_t n,
+                                int64_t l, int64_t ldx, pcc_prec prec,
+                                pcc_zmat **Z, void *stream);
 
 /* pcc_standardize for B FP32 matrices at once (Eq. 5 / Algorithm 3 applied
  * to each; the batching is this library's, for the many-datasets workload):
@@ -261,6 +277,18 @@ pcc_status pcc_cross_allpairs_host(const pcc_zmat *ZX, const pcc_zmat *ZY,
                                    int64_t device_bytes, pcc_rows_sink sink,
                                    void *user, void *stream);
 
+/* Bring an edge list to host memory: synchronises `stream`, stores the
+ * device count (*d_count, as written by the edge calls) in *count_host and
+ * copies the first min(count, capacity) records of `edges` (device) to
+ * edges_host (host, capacity records).  Returns PCC_ERR_CAPACITY when the
+ * count exceeds capacity (the records that fit are copied), else PCC_OK;
+ * PCC_ERR_INVALID_ARG for NULL d_count or count_host, or NULL edges /
+ * edges_host with capacity > 0.  The co-expression network of Section I,
+ * delivered to the host. */
+pcc_status pcc_edges_copy_host(const pcc_edge *edges, const uint64_t *d_count,
+                               uint64_t capacity, pcc_edge *edges_host,
+                               uint64_t *count_host, void *stream);
+
 /* Permutation test (Section IV-A): for permutations k in [k0, k1) of the P
  * given ones, r_k(i,j) = z_i . (z_j o pi_k) with (z_j o pi_k)[s] =
  * z_j[pi_k[s]] (only the second row of a pair is permuted); d_counts[J(i,j)]
@@ -305,6 +333,10 @@ pcc_status pcc_allpairs_upper_batched(const pcc_zmat *const *Zs, int32_t B,
  *             PCC_PREC_AUTO (tensor-core forms only).
  *   d_status  optional device int32 (caller-owned, may be NULL) set to 0 by
  *             the call and then to PCC_ERR_TIMEOUT if a device wait ran out.
+ *             With NULL the status goes to a word inside the array that no
+ *             call returns: a timeout is then not reported, and R may be
+ *             left partly written, so pass d_status wherever failures must
+ *             be seen.
  * Limit: 4 * n * lpad + n (rounded up to 256) + 256 <= 32 MiB, with lpad = l
  * rounded up to 64 (e.g. n = 16384 with l <= 448, or n = 8192 with l <=
  * 960); larger problems return PCC_ERR_INVALID_ARG.
@@ -324,9 +356,10 @@ pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
  * (paper_1605_01584_gb300/autotune.py); they affect later launches only and
  * never the result.  0 (or <= 0 for the costs) keeps a value.
  *   stage_k    K per shared-memory ring stage: 32 (4 stages; 6 in the 2-SM
- *              pair form, whose stages are a third smaller) or 64 (2).
- *   cluster    2 = CTA pairs that share the column operand by TMA
- *              multicast, 1 = independent CTAs.
+ *              pair form, whose stages are a third smaller) or 64 (2;
+ *              independent CTAs only).
+ *   cluster    2 = CTA pairs running one 2-SM MMA (while
+ *              pcc_set_pair_mma is on), 1 = independent CTAs.
  *   band_rows  super-tile rows per band of the pair schedule (rows of a
  *              band stay in L2 while column panels stream once per band).
  *   cost_c0, cost_c1  cost model of pcc_allpairs_upper_batched's work
@@ -341,14 +374,17 @@ pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
  * PCC_TC_PAIR=0 in the environment selects 0 when the library loads): two
  * CTAs run one 2-SM MMA (tcgen05.mma.cta_group::2, M = 256 rows over both),
  * each loading only half of the column operand, which the pair's tensor
- * cores exchange.
+ * cores exchange.  on = 0: independent CTAs, each loading its whole
+ * operands.  No form copies an operand to several CTAs (no TMA multicast).
  *   pcc_allpairs_upper / _edges / cross (cluster = 2, stage_k = 32): the
- *   pair computes one 256 x 256 super-tile; on = 0: each CTA runs its own
- *   M = 128 MMA and the column rows reach both CTAs by TMA multicast.
+ *   pair computes one 256 x 256 super-tile; on = 0: each CTA computes a
+ *   128 x 256 half on its own.
  *   pcc_perm_test: the pair computes two 128 x 128 tiles of one tile
  *   column, each CTA loading one of the two permutations of a pass; on = 0:
  *   independent CTAs, one tile each.
- * Affects later launches only; the results are the same.  Errors:
+ *   pcc_allpairs_upper_batched: CTA pairs take whole super-tiles; on = 0:
+ *   independent CTAs take halves.
+ * Affects later launches only; the results are the same bits.  Errors:
  * PCC_ERR_INVALID_ARG unless on is 0 or 1.  The paper has no counterpart
  * (a GB300 execution choice). */
 pcc_status pcc_set_pair_mma(int32_t on);
@@ -373,13 +409,21 @@ pcc_status pcc_measure_fp32_fma(double *tflops, void *stream);
  * status word and the kernel returns early instead of hanging. */
 pcc_status pcc_set_wait_limit_ns(uint64_t ns);
 
-/* Test hook for the failure path (the paper has no counterpart): while
- * enabled, the TMA producer of the tensor-core pair kernel issues no loads,
- * so every CTA's first operand wait runs out after the wait limit; the
- * kernel records PCC_ERR_TIMEOUT, frees its TMEM and returns, and the CUDA
- * context stays usable.  Nothing faults or hangs: no copy or MMA is in
- * flight when the CTAs unwind.  Pair with a short pcc_set_wait_limit_ns.
- * Never enable it outside tests. */
+/* Test hook for the failure path (the paper has no counterpart).
+ *   enable = 1  the TMA producer of the tensor-core pair kernel issues no
+ *               loads, so every CTA's first operand wait runs out after the
+ *               wait limit;
+ *   enable = 2  in the CTA-pair form only the odd CTA of each pair issues
+ *               none (the even CTA's copies land, its MMA waits for the
+ *               odd CTA's share and runs out);
+ *   enable = 3  only the even CTA issues none (the odd CTA's copies land on
+ *               barriers the even CTA never armed);
+ *   enable = 0  off.
+ * The kernel records PCC_ERR_TIMEOUT, waits (bounded) until every copy that
+ * was issued has landed, frees its TMEM and returns, and the CUDA context
+ * stays usable.  Nothing faults or hangs.  Pair with a short
+ * pcc_set_wait_limit_ns.  Never enable it outside tests.
+ * Errors: PCC_ERR_INVALID_ARG unless 0 <= enable <= 3. */
 pcc_status pcc_debug_drop_loads(int32_t enable);
 
 /* ------------------------------------------------------------------ */
@@ -400,6 +444,23 @@ pcc_status pcc_pair_coords(int64_t n, int64_t J, int64_t *i, int64_t *j);
 /* Eq. (17)-(19): tile id Jt in [0, m(m+1)/2) -> (yt, xt), yt <= xt, by the
  * same closed form plus correction the kernels use */
 pcc_status pcc_tile_coords(int64_t m, int64_t Jt, int64_t *yt, int64_t *xt);
+
+/* The tile schedule of the pair kernels, on the host (no device needed):
+ * pcc_schedule_num_tiles(n, prec) = pcc_num_tiles of a Z of n rows stored
+ * in form prec (AUTO resolved as pcc_standardize does), or -1 for n < 2 or
+ * a bad prec; pcc_schedule_tile_rect gives tile `tile`'s rows [row0, row1)
+ * and columns [col0, col1), clipped to n: the pairs i < j inside it are the
+ * ones pcc_allpairs_upper(Z, R, tile, tile + 1) writes.  Tensor-core forms
+ * follow the banded super-tile order with the current band_rows
+ * (pcc_set_tuning: keep it unchanged between computing and reading a tile
+ * range), the CUDA-core forms the triangular tile order of Eq. (17)-(19).
+ * This is how the ranks of Section III-D's distribution know which packed
+ * runs each of them wrote.  PCC_ERR_INVALID_ARG for an id out of range or a
+ * NULL pointer. */
+int64_t pcc_schedule_num_tiles(int64_t n, pcc_prec prec);
+pcc_status pcc_schedule_tile_rect(int64_t n, pcc_prec prec, int64_t tile,
+                                  int64_t *row0, int64_t *row1, int64_t *col0,
+                                  int64_t *col1);
 
 /* text of a status code (static storage) */
 const char *pcc_status_string(pcc_status s);

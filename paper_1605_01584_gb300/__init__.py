@@ -85,6 +85,9 @@ def load(path: str | None = None):
     sig = {
         "pcc_standardize": (_ST, [_P, _I32, _I64, _I64, _I64, _I32,
                                   ctypes.POINTER(_P), _P]),
+        "pcc_standardize_host": (_ST, [_P, _I32, _I64, _I64, _I64, _I32,
+                                       ctypes.POINTER(_P), _P]),
+        "pcc_edges_copy_host": (_ST, [_P, _P, _U64, _P, _P, _P]),
         "pcc_zmat_destroy": (_ST, [_P]),
         "pcc_standardize_batched": (_ST, [_P, _P, _P, _P, _I32, _I32, _P,
                                           _P]),
@@ -121,6 +124,8 @@ def load(path: str | None = None):
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
         "pcc_pair_coords": (_ST, [_I64, _I64, _P, _P]),
         "pcc_tile_coords": (_ST, [_I64, _I64, _P, _P]),
+        "pcc_schedule_num_tiles": (_I64, [_I64, _I32]),
+        "pcc_schedule_tile_rect": (_ST, [_I64, _I32, _I64, _P, _P, _P, _P]),
         "pcc_status_string": (ctypes.c_char_p, [_ST]),
     }
     for name, (res, args) in sig.items():
@@ -210,6 +215,36 @@ def pcc_standardize(X, prec="auto", Z: Zmat | None = None, stream=None,
     if Z is not None and h.value == Z.handle.value:
         return Z
     return Zmat(h.value)
+
+
+def pcc_standardize_host(X, prec="auto", Z: Zmat | None = None,
+                         stream=None) -> Zmat:
+    """Eq. (5) from a HOST matrix (torch CPU tensor, float32/64, 2-D with
+    unit inner stride; pin it for an asynchronous copy): the library copies
+    it to the device and standardizes it.  Reuses Z when it matches."""
+    import torch
+    assert not X.is_cuda and X.dim() == 2 and X.stride(1) == 1
+    xt = {torch.float32: PCC_F32, torch.float64: PCC_F64}[X.dtype]
+    h = ctypes.c_void_p(Z.handle.value if Z is not None else None)
+    _check(load().pcc_standardize_host(
+        _ptr(X), xt, X.shape[0], X.shape[1], X.stride(0), _prec(prec),
+        ctypes.byref(h), _stream(stream)), "pcc_standardize_host")
+    if Z is not None and h.value == Z.handle.value:
+        return Z
+    return Zmat(h.value)
+
+
+def pcc_edges_copy_host(edges, d_count, capacity: int, edges_host,
+                        stream=None) -> int:
+    """Copy the device edge list (uint8 buffer of pcc_edge records) and its
+    count to host memory (edges_host: CPU uint8 tensor of >= capacity*12
+    bytes); returns the count (PCC_ERR_CAPACITY raises)."""
+    c = _U64()
+    _check(load().pcc_edges_copy_host(_ptr(edges), _ptr(d_count),
+                                      int(capacity), _ptr(edges_host),
+                                      ctypes.byref(c), _stream(stream)),
+           "pcc_edges_copy_host")
+    return int(c.value)
 
 
 def pcc_standardize_batched(Xs, prec="auto", Zs=None, stream=None):
@@ -432,16 +467,17 @@ def pcc_set_wait_limit_ns(ns: int):
     _check(load().pcc_set_wait_limit_ns(int(ns)), "pcc_set_wait_limit_ns")
 
 
-def pcc_debug_drop_loads(enable: bool):
-    """Test hook: make the pair kernel's operand waits run out (see pcc.h)."""
-    _check(load().pcc_debug_drop_loads(1 if enable else 0),
-           "pcc_debug_drop_loads")
+def pcc_debug_drop_loads(enable):
+    """Test hook: make the pair kernel's operand waits run out (see pcc.h).
+    True/1: no producer issues loads; 2 / 3: only the odd / even CTA of each
+    CTA pair issues none."""
+    _check(load().pcc_debug_drop_loads(int(enable)), "pcc_debug_drop_loads")
 
 
 def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,
                    cost_c1=0.0, pair_mma=None):
-    """Zeros (and pair_mma=None) keep a value; pair_mma 1/0 selects the
-    2-SM MMA or the multicast form of the CTA pairs (pcc_set_pair_mma)."""
+    """Zeros (and pair_mma=None) keep a value; pair_mma 1/0 selects CTA
+    pairs running one 2-SM MMA or independent CTAs (pcc_set_pair_mma)."""
     _check(load().pcc_set_tuning(int(stage_k), int(cluster), int(band_rows),
                                  float(cost_c0), float(cost_c1)),
            "pcc_set_tuning")
@@ -488,6 +524,19 @@ def pcc_tile_coords(m: int, Jt: int):
     _check(load().pcc_tile_coords(m, Jt, ctypes.byref(y), ctypes.byref(x)),
            "pcc_tile_coords")
     return y.value, x.value
+
+
+def pcc_schedule_num_tiles(n: int, prec="auto") -> int:
+    return int(load().pcc_schedule_num_tiles(int(n), _prec(prec)))
+
+
+def pcc_schedule_tile_rect(n: int, prec, tile: int):
+    """(row0, row1, col0, col1) of a tile of the pair schedule (host)."""
+    v = [_I64() for _ in range(4)]
+    _check(load().pcc_schedule_tile_rect(int(n), _prec(prec), int(tile),
+                                         *[ctypes.byref(x) for x in v]),
+           "pcc_schedule_tile_rect")
+    return tuple(x.value for x in v)
 
 
 def pcc_status_string(s: int) -> str:

@@ -2,11 +2,10 @@
 
 The knobs never change results, only speed:
   stage_k    K per shared-memory ring stage (32: 4 stages, 6 in the 2-SM
-             pair form; 64: 2 stages)
-  cluster    2 = CTA pairs sharing the column operand by TMA multicast,
-             1 = independent CTAs
-  pair_mma   with CTA pairs and stage_k 32: 1 = one 2-SM MMA per pair
-             (each CTA loads half of the column operand), 0 = multicast
+             pair form; 64: 2 stages, independent CTAs only)
+  pair_mma   1 = CTA pairs running one 2-SM MMA (each CTA loads half of
+             the column operand; stage_k 32), 0 = independent CTAs; the
+             cluster knob follows it (2 with pairs, 1 without)
   band_rows  super-tile rows per band of the pair schedule
 and the batched work split's cost model (cycles per unit c0, per K block and
 product c1).
@@ -33,7 +32,6 @@ from . import (PccError, load, pcc_allpairs_upper, pcc_get_tuning,
 
 DEFAULT_CANDIDATES = {
     "stage_k": (32, 64),
-    "cluster": (2, 1),
     "pair_mma": (1, 0),
     "band_rows": (16, 32, 64),
 }
@@ -145,12 +143,12 @@ def tune_pairs(n: int, l: int, prec: str = "auto", candidates=None,
     before = pcc_get_tuning()
     results = []
     try:
-        for sk, cl, pm, bd in itertools.product(
-                cand["stage_k"], cand["cluster"], cand["pair_mma"],
-                cand["band_rows"]):
-            # the pair form only differs for CTA pairs with K = 32 stages
-            if pm != cand["pair_mma"][0] and not (cl == 2 and sk == 32):
+        for sk, pm, bd in itertools.product(
+                cand["stage_k"], cand["pair_mma"], cand["band_rows"]):
+            # the 2-SM pair form runs with K = 32 stages only
+            if pm and sk != 32:
                 continue
+            cl = 2 if pm else 1
             pcc_set_tuning(stage_k=sk, cluster=cl, band_rows=bd, pair_mma=pm)
             ms = _time_ms(lambda: pcc_allpairs_upper(Z, R), reps)
             results.append({"stage_k": sk, "cluster": cl, "pair_mma": pm,

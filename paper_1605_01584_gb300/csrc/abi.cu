@@ -52,20 +52,17 @@ bool device_is_sm103(int dev) {
 }  // namespace
 
 pcc_prec resolve_prec(pcc_prec p, int64_t l) {
-  // Both split forms cost the same.  Their error has two parts: how well
-  // the two halves represent z (FP16 halves of z 2^s: ~2^-22 relative;
-  // BF16 halves: ~2^-18) and the tensor cores' FP32 accumulation, which
-  // rounds toward zero at every update and loses more with FP16 halves.
-  // On rows with planted modules BF16X3 is slightly better; on exact
-  // copies of rows whose mass sits in one sample (r = 1, nothing averages
-  // out) the representation dominates and BF16X3 reaches 1.0-1.3e-5 at
-  // every l, while FP16X3S stays at <= 9.1e-6 up to l = 2048 (two
-  // accumulators above l = 1024).  Max |dr| of the two studies, measured:
-  //   l      256      512      1024     2048     3072     4096
-  //   FP16   2.1e-6   4.7e-6   9.1e-6   8.9e-6   1.25e-5  1.76e-5
-  //   BF16   1.26e-5  1.25e-5  1.20e-5  1.05e-5  1.34e-5  1.88e-5
+  // Both 3-product split forms cost the same.  Their error has two parts:
+  // how well the two halves represent z (FP16 halves of z 2^s: ~2^-22
+  // relative; BF16 halves: ~2^-18) and the tensor cores' FP32 accumulation,
+  // which rounds its running sum toward zero at every update.  Accumulating
+  // long rows in chunks of at most 640 samples (tc_common.cuh) bounds the
+  // second part at every l, so the representation decides: on exact copies
+  // of rows whose mass sits in one sample (r = 1, nothing averages out)
+  // BF16X3 reaches 1.0-1.3e-5 at every l while FP16X3S stays below 1e-5.
+  (void)l;
   if (p != PCC_PREC_AUTO) return p;
-  return l <= 2048 ? PCC_PREC_FP16X3S : PCC_PREC_BF16X3;
+  return PCC_PREC_FP16X3S;
 }
 
 namespace {
@@ -98,7 +95,7 @@ uint64_t wait_limit_ns() { return g_wait_ns.load(); }
 namespace {
 std::atomic<int> g_drop_loads{0};
 }
-bool debug_drop_loads() { return g_drop_loads.load() != 0; }
+int debug_drop_loads() { return g_drop_loads.load(); }
 
 namespace {
 std::mutex g_tune_mu;
@@ -115,12 +112,24 @@ TcTuning g_tune = [] {
   t.band = (v >= 1 && v <= 4096) ? v : 32;
   t.cost_c0 = 3000.0;
   t.cost_c1 = 260.0;
-  e = getenv("PCC_TC_KALT");
-  const int ka = e ? atoi(e) : 0;
-  t.kalt_min_l = ka >= 64 ? ka : 1024;
+  e = getenv("PCC_TC_ONEACC");
+  const int oa = e ? atoi(e) : 0;
+  t.one_acc_l = oa >= 64 ? oa : 1024;
+  e = getenv("PCC_TC_CHUNK");
+  const int ch = e ? atoi(e) : 0;
+  t.chunk_l = ch >= 64 ? ch : 640;
   return t;
 }();
 }  // namespace
+
+int accum_chunks(int64_t lpad, int nkb) {
+  const TcTuning t = tc_tuning();
+  if (lpad <= t.one_acc_l || nkb < 2) return 1;
+  int64_t c = (lpad + t.chunk_l - 1) / t.chunk_l;
+  if (c < 2) c = 2;
+  if (c > nkb) c = nkb;
+  return (int)c;
+}
 
 TcTuning tc_tuning() {
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -291,6 +300,73 @@ pcc_status pcc_standardize(const void* X, pcc_dtype xt, int64_t n, int64_t l,
                                         static_cast<cudaStream_t>(stream)));
 }
 
+pcc_status pcc_standardize_host(const void* X_host, pcc_dtype xt, int64_t n,
+                                int64_t l, int64_t ldx, pcc_prec prec,
+                                pcc_zmat** Z, void* stream) {
+  if (!X_host || !Z || n < 2 || l < 2 || ldx < l || n >= (1ll << 31) ||
+      l >= (1ll << 31) || (xt != PCC_F32 && xt != PCC_F64) ||
+      (int)prec < 0 || prec > PCC_PREC_AUTO)
+    return PCC_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PCC_ERR_CUDA;
+  const pcc_prec rp = resolve_prec(prec, l);
+  if (is_split(rp) && !device_is_sm103(dev)) return PCC_ERR_UNSUPPORTED;
+  if (!zmat_matches(*Z, dev, n, l, rp)) {
+    pcc_zmat* nz = nullptr;
+    pcc_status st = zmat_create(dev, n, l, rp, &nz);
+    if (st != PCC_OK) return st;
+    *Z = nz;
+  }
+  pcc_zmat* z = *Z;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t es = xt == PCC_F64 ? 8 : 4;
+  const size_t need = (size_t)n * (size_t)l * es;
+  if (z->xin_ws_bytes < need) {
+    if (z->xin_ws) {
+      // the previous call's copy may still be read on its stream
+      if (cudaStreamSynchronize(s) != cudaSuccess) return PCC_ERR_CUDA;
+      cudaFree(z->xin_ws);
+      z->xin_ws = nullptr;
+      z->xin_ws_bytes = 0;
+    }
+    if (cudaMalloc(&z->xin_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return PCC_ERR_OOM;
+    }
+    z->xin_ws_bytes = need;
+  }
+  cudaError_t e =
+      ldx == l ? cudaMemcpyAsync(z->xin_ws, X_host, need,
+                                 cudaMemcpyHostToDevice, s)
+               : cudaMemcpy2DAsync(z->xin_ws, (size_t)l * es, X_host,
+                                   (size_t)ldx * es, (size_t)l * es, (size_t)n,
+                                   cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(launch_standardize(z->xin_ws, xt, l, z, s));
+}
+
+pcc_status pcc_edges_copy_host(const pcc_edge* edges, const uint64_t* d_count,
+                               uint64_t capacity, pcc_edge* edges_host,
+                               uint64_t* count_host, void* stream) {
+  if (!d_count || !count_host || (capacity > 0 && (!edges || !edges_host)))
+    return PCC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint64_t c = 0;
+  if (cudaMemcpyAsync(&c, d_count, sizeof(c), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return PCC_ERR_CUDA;
+  *count_host = c;
+  const uint64_t k = c < capacity ? c : capacity;
+  if (k > 0) {
+    if (cudaMemcpyAsync(edges_host, edges, k * sizeof(pcc_edge),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return PCC_ERR_CUDA;
+  }
+  return c > capacity ? PCC_ERR_CAPACITY : PCC_OK;
+}
+
 pcc_status pcc_standardize_batched(const float* const* Xs, const int64_t* ns,
                                    const int64_t* ls, const int64_t* ldxs,
                                    int32_t B, pcc_prec prec, pcc_zmat** Zs,
@@ -326,6 +402,7 @@ pcc_status pcc_zmat_destroy(pcc_zmat* Z) {
   if (Z->perm_ws) cudaFree(Z->perm_ws);
   if (Z->win_ws) cudaFree(Z->win_ws);
   if (Z->stage_ws) cudaFreeHost(Z->stage_ws);
+  if (Z->xin_ws) cudaFree(Z->xin_ws);
   cudaError_t e = cudaFree(Z->base);
   if (cur != Z->device) cudaSetDevice(cur);
   free(Z);
@@ -360,6 +437,42 @@ int64_t pcc_num_tiles(const pcc_zmat* Z) {
   const int64_t t = simt_tile_size(Z->prec);
   const int64_t m = (Z->n + t - 1) / t;
   return m * (m + 1) / 2;
+}
+
+int64_t pcc_schedule_num_tiles(int64_t n, pcc_prec prec) {
+  if (n < 2 || (int)prec < 0 || prec > PCC_PREC_AUTO) return -1;
+  const pcc_prec rp = resolve_prec(prec, 2);
+  if (is_split(rp)) return tc_num_tiles(n);
+  const int64_t t = simt_tile_size(rp);
+  const int64_t m = (n + t - 1) / t;
+  return m * (m + 1) / 2;
+}
+
+pcc_status pcc_schedule_tile_rect(int64_t n, pcc_prec prec, int64_t tile,
+                                  int64_t* row0, int64_t* row1,
+                                  int64_t* col0, int64_t* col1) {
+  const int64_t T = pcc_schedule_num_tiles(n, prec);
+  if (T < 0 || tile < 0 || tile >= T || !row0 || !row1 || !col0 || !col1)
+    return PCC_ERR_INVALID_ARG;
+  const pcc_prec rp = resolve_prec(prec, 2);
+  int64_t yt, xt, side;
+  if (is_split(rp)) {
+    // the banded super-tile order of the tensor-core kernels
+    const int64_t m = tc_super_count(n), G = tc_tuning().band;
+    BandCursor cur;
+    band_cursor_init(&cur, m, G);
+    band_tile_coords(&cur, m, G, tile, &yt, &xt);
+    side = kTcSuper;
+  } else {
+    // Eq. (17)-(19) over the CUDA-core kernels' tiles
+    side = simt_tile_size(rp);
+    tri_coords((n + side - 1) / side, tile, &yt, &xt);
+  }
+  *row0 = yt * side;
+  *row1 = (yt + 1) * side < n ? (yt + 1) * side : n;
+  *col0 = xt * side;
+  *col1 = (xt + 1) * side < n ? (xt + 1) * side : n;
+  return PCC_OK;
 }
 
 pcc_status pcc_allpairs_upper(const pcc_zmat* Z, void* R, pcc_dtype rt,
@@ -566,7 +679,8 @@ pcc_status pcc_sync_status(pcc_zmat* Z, void* stream) {
 }
 
 pcc_status pcc_debug_drop_loads(int32_t enable) {
-  g_drop_loads.store(enable ? 1 : 0);
+  if (enable < 0 || enable > 3) return PCC_ERR_INVALID_ARG;
+  g_drop_loads.store(enable);
   return PCC_OK;
 }
 

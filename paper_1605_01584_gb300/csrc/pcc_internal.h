@@ -34,6 +34,9 @@ struct pcc_zmat {
   size_t win_ws_bytes;
   void* stage_ws;
   size_t stage_ws_bytes;
+  // device copy of a host input (pcc_standardize_host), kept between calls
+  void* xin_ws;
+  size_t xin_ws_bytes;
 };
 
 namespace pcc {
@@ -51,7 +54,9 @@ inline int device_slot(int device) {
   return device < 0 ? 0 : (device < kDeviceSlots ? device : kDeviceSlots - 1);
 }
 uint64_t wait_limit_ns();
-bool debug_drop_loads();  // test hook of pcc_debug_drop_loads
+// test hook of pcc_debug_drop_loads: 0 off, 1 every producer, 2 the odd
+// CTA of each pair, 3 the even CTA of each pair
+int debug_drop_loads();
 cudaError_t ensure_func_smem(const void* func, int bytes);
 pcc_status cuda_status(cudaError_t e);
 
@@ -66,20 +71,26 @@ bool encode_tmap_3d_u16(CUtensorMap* map, const void* base, int64_t depth,
                         bool bf16);
 
 // Knobs of the tensor-core kernels (the tuner's choices).  Initial values
-// come from PCC_TC_BK, PCC_TC_CLUSTER, PCC_TC_BAND; pcc_set_tuning changes
-// them for later launches.
+// come from PCC_TC_BK, PCC_TC_CLUSTER, PCC_TC_PAIR, PCC_TC_BAND,
+// PCC_TC_ONEACC, PCC_TC_CHUNK; pcc_set_tuning changes them for later
+// launches.
 struct TcTuning {
   int stage_k;       // K per ring stage: 32 or 64
-  int cluster;       // 2 = CTA pairs sharing B by multicast, 1 = single CTAs
-  int pair_mma;      // with cluster 2: the pair runs one 2-SM MMA (M = 256)
-                     // and each CTA loads only its half of B
+  int cluster;       // 2 = CTA pairs (with pair_mma), 1 = single CTAs
+  int pair_mma;      // CTA pairs run one 2-SM MMA (M = 256), each CTA
+                     // loading only its half of B; 0 = single CTAs
   int64_t band;      // super-tile rows per band of the pair schedule
   double cost_c0;    // batched plan: cycles per unit outside the K loop
   double cost_c1;    // batched plan: cycles per K block and product
-  int64_t kalt_min_l;  // padded rows longer than this use two accumulators
+  int64_t one_acc_l;  // padded rows up to this length use one accumulator
+  int64_t chunk_l;    // longer rows: accumulator chunks of at most this
 };
 TcTuning tc_tuning();
 void tc_set_tuning(const TcTuning& t);
+// Accumulator chunks of a work unit with padded rows of lpad samples in nkb
+// K blocks (tc_common.cuh): 1 up to one_acc_l samples, else enough chunks of
+// at most chunk_l samples (at least 2, at most nkb).
+int accum_chunks(int64_t lpad, int nkb);
 
 // K1: standardize rows of X into Z's storage.
 cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,

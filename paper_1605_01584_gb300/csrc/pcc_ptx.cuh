@@ -42,6 +42,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
                : "memory");
 }
 
+// Lower the pending transaction count of the current phase of `bar` by
+// `bytes` without a copy: cancels the share of bytes a peer announced
+// but never sent (the pair form's drain after an abort).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar,
+                                                 uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -126,21 +137,6 @@ __device__ __forceinline__ void tma_load_2d_hint(void* dst,
       : "memory");
 }
 
-// 2-D tiled load delivered to every CTA of `mask` in the cluster (same
-// shared-memory offset for the data and the mbarrier in each of them).
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* m,
-                                               uint64_t* bar, int32_t c0,
-                                               int32_t c1, uint16_t mask,
-                                               uint64_t pol) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_"
-      "tx::bytes.multicast::cluster.L2::cache_hint [%0], [%1, {%3, %4}], [%2], "
-      "%5, %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(c0),
-      "r"(c1), "h"(mask), "l"(pol)
-      : "memory");
-}
-
 // All threads of all CTAs of the cluster (release/acquire).
 __device__ __forceinline__ void cluster_sync() {
   asm volatile(
@@ -218,16 +214,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// As umma_commit, arriving on the mbarrier at the same offset in every CTA
-// of `mask`.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster."
-      "multicast::cluster.b64 [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
 // ------------------------------------------- 2-SM MMA (CTA pair forms)
 // The CTAs of a cluster of two act as one MMA unit: M = 256 rows, the
 // first 128 from the even CTA's shared memory and accumulated in its TMEM,
@@ -244,6 +230,12 @@ __device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
                : "=r"(r)
                : "r"(smem_u32(p)), "r"(rank));
   return r;
+}
+
+// 32-bit store into another CTA's shared memory (shared::cluster address).
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v)
+               : "memory");
 }
 
 // Arrive on an mbarrier given by its shared::cluster address (another CTA).
@@ -378,6 +370,22 @@ __device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr,
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
       "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
       "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr,
+                                                   const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+      "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+      "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]),
+      "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]),
+      "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]),
+      "r"(v[30]), "r"(v[31])
       : "memory");
 }
 

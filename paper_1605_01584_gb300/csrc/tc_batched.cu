@@ -12,8 +12,8 @@
 // per matrix at run time, so one kernel serves the whole batch.
 //
 // Same roles, pipeline and bounded waits as the single-matrix kernel
-// (tc_pairs.cu), K = 32 per stage; matrices with rows longer than 1024 split
-// their K blocks over two accumulators as that kernel does.  With the pair
+// (tc_pairs.cu), K = 32 per stage; matrices with rows longer than 1024
+// accumulate their units in chunks as that kernel does (tc_common.cuh).  With the pair
 // form (pcc_set_pair_mma, the default) the plan hands whole super-tiles to
 // CTA pairs, which run one 2-SM MMA per tile (M = 256, each CTA loading its
 // 128 A rows and 128 of the B rows, as in tc_pairs.cu); otherwise single
@@ -29,6 +29,7 @@
 #include "pcc_internal.h"
 #include "pcc_ptx.cuh"
 #include "pcc_sched.h"
+#include "tc_common.cuh"
 #include "tc_epilogue.cuh"
 
 namespace pcc {
@@ -44,8 +45,9 @@ struct BCfg {
   static constexpr int kTileB = (PAIR ? kBM : kBN) * kKB * 2;
   static constexpr int kStageBytes = 2 * (kTileA + kTileB);  // 3 products
   static constexpr int kStages = PAIR ? 6 : 4;
+  static constexpr int kBarBytes = 512;
   static constexpr int kSmemBytes =
-      1024 + kStages * kStageBytes + kEpiBytes + 256;
+      1024 + kStages * kStageBytes + kEpiBytes + kBarBytes;
   static_assert(kSmemBytes <= 232448, "shared memory budget");
 };
 
@@ -58,8 +60,7 @@ struct MatDesc {
   int64_t m;          // super-tiles per side
   int nkb;            // K blocks of 32
   int nprod;          // 4, 3 or 1 products per K step
-  int kalt;           // the two halves of the K blocks in two accumulators
-                      // (long rows)
+  int nch;            // accumulator chunks per unit (tc_common.cuh)
   uint32_t idesc;     // MMA instruction descriptor (BF16 or FP16 halves)
   float scale;        // accumulator -> r
   const uint8_t* flags;
@@ -100,6 +101,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* mdone = tempty + 2;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  FillLog* flog = reinterpret_cast<FillLog*>(bars + 32);
+  static_assert(2 * kStages + 5 <= 31, "barrier area");
+  static_assert(32 * 8 + sizeof(FillLog) <= C::kBarBytes, "barrier area");
   auto sA_hi = [&](int s) { return ring + s * kStageBytes; };
   auto sB_hi = [&](int s) { return ring + s * kStageBytes + kTileA; };
   auto sA_lo = [&](int s) { return ring + s * kStageBytes + kTileA + kTileB; };
@@ -121,6 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(mdone, 1);
     *abort_flag = 0;
+    fill_log_init(flog);
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -171,8 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t pol = l2_policy_evict_last();
       Walk wk;
       int stage = 0;
-      uint32_t phase = 0, issued_mask = 0, last_phase[kStages];
-      for (int s = 0; s < kStages; ++s) last_phase[s] = 0;
+      uint32_t phase = 0;
       bool ok = true;
       for (int64_t it = it0; it < it1 && ok; ++it) {
         const MatDesc* d;
@@ -217,21 +221,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                                kc, (int)col0 + kBM, pol);
             }
           }
-          issued_mask |= 1u << stage;
-          last_phase[stage] = phase;
+          flog->fills[stage] += 1u;
+          flog->bytes[stage] = bytes;
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1u;
           }
         }
       }
-      // drain (PAIR: the even CTA's barriers count both CTAs' copies)
-      WaitCtx wd = w;
-      volatile int never = 0;
-      wd.abort_flag = &never;
-      if (!PAIR || crank == 0)
-        for (int s = 0; s < kStages; ++s)
-          if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
     }
   } else if (warp == 1) {
     // MMA issuer (PAIR: the even CTA issues for both)
@@ -244,79 +241,64 @@ __global__ void __launch_bounds__(kThreads, 1)
         const MatDesc* d;
         int64_t row0, col0;
         coords(wk, p.items[it], d, &row0, &col0);
-        const int nkb = d->nkb, nprod = d->nprod, kalt = d->kalt;
+        const int nkb = d->nkb, nprod = d->nprod, nch = d->nch;
         const uint32_t idesc = d->idesc;
-        if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
-        const int acc0 = acc;
-        uint32_t aph1 = aphase;
-        if (kalt) {
-          // the second half of the K blocks goes to the other buffer,
-          // awaited only there (as in tc_pairs.cu)
-          acc ^= 1;
-          if (acc == 0) aphase ^= 1u;
-          aph1 = aphase;
-        }
-        tc_fence_after();
-        const uint32_t d_tmem0 = tmem_base + (uint32_t)(acc0 * kBN);
-        const uint32_t d_tmem1 = tmem_base + (uint32_t)(acc * kBN);
-        const int khalf = kalt ? nkb / 2 : nkb;
-        for (int kb = 0; kb < nkb; ++kb) {
-          if (kalt && kb == khalf) {
-            if (!mbar_wait(&tempty[acc], aph1 ^ 1u, w)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
-          const uint32_t d_tmem = (kalt && kb >= khalf) ? d_tmem1 : d_tmem0;
-          const uint32_t first = kb == 0 || kb == khalf;
-          if (!mbar_wait(&full[stage], phase, w)) {
+        for (int c = 0; c < nch && ok; ++c) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t aH = smem_u32(sA_hi(stage));
-          const uint32_t bH = smem_u32(sB_hi(stage));
-          const uint32_t aL = smem_u32(sA_lo(stage));
-          const uint32_t bL = smem_u32(sB_lo(stage));
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kBN);
+          const int kb0 = chunk_begin(nkb, nch, c);
+          const int kb1 = chunk_begin(nkb, nch, c + 1);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(&full[stage], phase, w)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t aH = smem_u32(sA_hi(stage));
+            const uint32_t bH = smem_u32(sB_hi(stage));
+            const uint32_t aL = smem_u32(sA_lo(stage));
+            const uint32_t bL = smem_u32(sB_lo(stage));
 #pragma unroll
-          for (int ks = 0; ks < kKB / kUK; ++ks) {
-            const uint32_t off = ks * kUK * 2;
-            const uint64_t dAH = kmajor_desc<64>(aH + off);
-            const uint64_t dBH = kmajor_desc<64>(bH + off);
-            auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
-              if constexpr (PAIR)
-                umma_f16_pair(d_tmem, a, b, idesc, acc_in);
-              else
-                umma_f16(d_tmem, a, b, idesc, acc_in);
-            };
-            mma(dAH, dBH, (first && ks == 0) ? 0u : 1u);
-            if (nprod >= 3) {
-              mma(dAH, kmajor_desc<64>(bL + off), 1u);
-              mma(kmajor_desc<64>(aL + off), dBH, 1u);
-              if (nprod == 4)
-                mma(kmajor_desc<64>(aL + off), kmajor_desc<64>(bL + off), 1u);
+            for (int ks = 0; ks < kKB / kUK; ++ks) {
+              const uint32_t off = ks * kUK * 2;
+              const uint64_t dAH = kmajor_desc<64>(aH + off);
+              const uint64_t dBH = kmajor_desc<64>(bH + off);
+              auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
+                if constexpr (PAIR)
+                  umma_f16_pair(d_tmem, a, b, idesc, acc_in);
+                else
+                  umma_f16(d_tmem, a, b, idesc, acc_in);
+              };
+              mma(dAH, dBH, (kb == kb0 && ks == 0) ? 0u : 1u);
+              if (nprod >= 3) {
+                mma(dAH, kmajor_desc<64>(bL + off), 1u);
+                mma(kmajor_desc<64>(aL + off), dBH, 1u);
+                if (nprod == 4)
+                  mma(kmajor_desc<64>(aL + off), kmajor_desc<64>(bL + off),
+                      1u);
+              }
+            }
+            if constexpr (PAIR)
+              umma_commit_pair(&empty[stage], 3);  // frees it in both CTAs
+            else
+              umma_commit(&empty[stage]);
+            if (++stage == kStages) {
+              stage = 0;
+              phase ^= 1u;
             }
           }
+          if (!ok) break;
           if constexpr (PAIR)
-            umma_commit_pair(&empty[stage], 3);  // frees it in both CTAs
+            umma_commit_pair(&tfull[acc], 3);
           else
-            umma_commit(&empty[stage]);
-          if (++stage == kStages) {
-            stage = 0;
-            phase ^= 1u;
-          }
+            umma_commit(&tfull[acc]);
+          acc ^= 1;
+          if (acc == 0) aphase ^= 1u;
         }
-        if (!ok) break;
-        if constexpr (PAIR) {
-          umma_commit_pair(&tfull[acc0], 3);
-          if (kalt) umma_commit_pair(&tfull[acc], 3);
-        } else {
-          umma_commit(&tfull[acc0]);
-          if (kalt) umma_commit(&tfull[acc]);
-        }
-        acc ^= 1;
-        if (acc == 0) aphase ^= 1u;
       }
       if constexpr (PAIR)
         umma_commit_pair(mdone, 1);
@@ -334,6 +316,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     Walk wk;
     int acc = 0;
     uint32_t aphase = 0;
+    // release a TMEM buffer to the MMA issuer (PAIR: the even CTA's)
+    auto release = [&](int a) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR && crank != 0)
+          mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
+        else
+          mbar_arrive(&tempty[a]);
+      }
+    };
     for (int64_t it = it0; it < it1; ++it) {
       const MatDesc* d;
       int64_t row0, col0;
@@ -350,63 +343,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         cfl[c] = (jj < n) ? d->flags[jj] : 1;
       }
       const EpiOut eo{d->R, d->scale, 2.f, nullptr, nullptr, 0, p.status};
-      const int kalt = d->kalt;
-      bool okw = true;
-      const int acc0 = acc;
-      if (lane == 0) okw = mbar_wait(&tfull[acc], aphase, w);
-      if (kalt) {
-        acc ^= 1;
-        if (acc == 0) aphase ^= 1u;
-        if (lane == 0 && okw) okw = mbar_wait(&tfull[acc], aphase, w);
-      }
-      if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) break;
-      tc_fence_after();
-      const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
-      const int64_t base0 = pair_row_base(n, rbase);
       const uint32_t lane_off =
           ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
-      const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
-      // release a TMEM buffer to the MMA issuer (PAIR: the even CTA's)
-      auto release = [&](int a) {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if (PAIR && crank != 0)
-            mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
-          else
-            mbar_arrive(&tempty[a]);
+      // chunks: each finished chunk is added into the next one
+      int last = -1;
+      bool ok = true;
+      for (int c = 0; c < d->nch; ++c) {
+        bool okw = true;
+        if (lane == 0) okw = mbar_wait(&tfull[acc], aphase, w);
+        if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) {
+          ok = false;
+          break;
         }
-      };
-      uint32_t t_out = t_row;
-      if (kalt) {
-        // fold the first half's accumulator into the second's and free it
-        t_out = tmem_base + lane_off + (uint32_t)(acc * kBN);
-        fold_acc(t_row, t_out);
-        release(acc0);
+        tc_fence_after();
+        if (last >= 0) {
+          fold_acc(tmem_base + lane_off + (uint32_t)(last * kBN),
+                   tmem_base + lane_off + (uint32_t)(acc * kBN));
+          release(last);
+        }
+        last = acc;
+        acc ^= 1;
+        if (acc == 0) aphase ^= 1u;
       }
-      epilogue_rows<true, false>(t_out, stg, lane, n, rbase, jw0, base0,
-                                 rflags, cfl, eo);
-      release(kalt ? acc : acc0);
-      acc ^= 1;
-      if (acc == 0) aphase ^= 1u;
+      if (!ok) break;
+      const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
+      const int64_t base0 = pair_row_base(n, rbase);
+      epilogue_rows<true, false>(tmem_base + lane_off + (uint32_t)(last * kBN),
+                                 stg, lane, n, rbase, jw0, base0, rflags, cfl,
+                                 eo);
+      release(last);
     }
   }
 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if constexpr (PAIR) {
-    // after an abort, the odd CTA's last copies are counted on barriers no
-    // one waits for any more: give them time to land (bounded, error path)
-    if (*abort_flag && threadIdx.x == 0) {
-      const uint64_t t0 = global_timer_ns();
-      while (global_timer_ns() - t0 < 200000u) {
-      }
-    }
-    __syncthreads();
-    // neither CTA leaves while the other may still use its memory or TMEM
-    cluster_sync();
-  }
+  // every copy issued by this CTA (PAIR: by either CTA) has landed before
+  // a CTA of the pair may exit
+  drain_ring<PAIR>(full, nullptr, flog, kStages, w, crank);
   if (warp == 1) {
     __syncwarp();
     if constexpr (PAIR)
@@ -486,7 +460,7 @@ bool build_plan(Plan* P) {
     d.nprod = Z->prec == PCC_PREC_BF16X1   ? 1
               : Z->prec == PCC_PREC_BF16X4 ? 4
                                            : 3;
-    d.kalt = (Z->lpad > tc_tuning().kalt_min_l && d.nkb >= 2) ? 1 : 0;
+    d.nch = accum_chunks(Z->lpad, d.nkb);
     // the pair form's one instruction covers both CTAs' 128 rows
     d.idesc =
         make_idesc_f16(Z->prec != PCC_PREC_FP16X3S, pair ? 2 * kBM : kBM, kBN);
@@ -580,6 +554,8 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
       bool same = q->tuning.band == tc_tuning().band &&
                   q->tuning.cost_c0 == tc_tuning().cost_c0 &&
                   q->tuning.cost_c1 == tc_tuning().cost_c1 &&
+                  q->tuning.one_acc_l == tc_tuning().one_acc_l &&
+                  q->tuning.chunk_l == tc_tuning().chunk_l &&
                   q->pair == (tc_tuning().pair_mma != 0);
       for (int b = 0; b < B && same; ++b)
         same = q->zs[b] == Zs[b] && q->rs[b] == Rs[b] &&

@@ -14,15 +14,9 @@
 // another): every (i < n, j < ncol) is a pair, and row i of R starts at
 // base0 + (i - rbase) * ldr.
 //
-// Why two accumulators for long rows: the tensor cores' FP32 accumulation
-// rounds every update toward zero, so its error grows with the number of
-// updates into a large partial sum (measured: 1.2e-5 on |r| ~ 1 at l = 2048
-// with one accumulator, always toward smaller |r|).  Giving each of two
-// accumulators half of the K blocks halves both the updates and the partial
-// sum of each, and their sum is formed with round-to-nearest: fold_acc adds
-// the first accumulator into the second in TMEM, so that the first buffer
-// is released (and the next unit's first half can run in it) before the
-// store pass over the second.
+// Long rows: the K blocks of a unit are accumulated in chunks (see
+// tc_common.cuh); fold_acc adds a finished chunk into the next one in TMEM
+// so that the chunk's buffer can be handed back before the store pass.
 #pragma once
 #include <stdint.h>
 

@@ -30,11 +30,10 @@
 //               contiguous), clamp to [-1,1], NaN for flagged rows, and the
 //               optional warp-aggregated edge append.
 // The two accumulators let the epilogue of one unit overlap the MMAs of the
-// next.  Rows longer than 1,024 samples (kalt) split a unit's K blocks in
-// two halves, one per accumulator: the FP32 accumulation rounds its running
-// sum toward zero, and halving each sum's length halves that bias.  The
-// epilogue adds the first accumulator into the second in TMEM (fold_acc),
-// releases the first to the next unit at once, and stores from the second.
+// next.  Rows longer than 1,024 samples cut a unit's K blocks into chunks
+// of at most 640 samples, each accumulated in a fresh buffer and added into
+// the next by the epilogue (tc_common.cuh): the FP32 accumulation rounds
+// its running sum toward zero, and a shorter running sum loses less.
 //
 // CROSS: the non-symmetric job matrix between the rows of two matrices
 // (Section III-B, Eq. (7)-(8)): A rows come from the first, B rows from the
@@ -45,24 +44,20 @@
 // stay in L2 while B streams past them once.
 //
 // CTA pairs (the default: 2-CTA clusters).  The CTAs of a pair compute the
-// two halves of one super-tile, which need the same 256 B rows.
-//   PAIR (the default, K = 32 stages): the pair is one 2-SM MMA unit.  Each
-//     CTA loads its 128 A rows and 128 of the B rows into its own stage, and
-//     the even CTA issues tcgen05.mma.cta_group::2 with M = 256: the pair's
-//     tensor cores exchange the B halves, so each SM takes a third less
-//     operand data from L2 than with multicast, and a stage is a third
-//     smaller (six stages instead of four).  Both CTAs' copies count on the
-//     even CTA's stage barrier; its commits release the stage in both CTAs
-//     and hand each CTA its half of the accumulator; both epilogues release
-//     the accumulator to the even CTA.
-//   otherwise: each CTA runs its own M = 128 MMA; each loads 128 of the B
-//     rows and multicasts them to both, and both MMAs must release a stage
-//     before either producer refills it.
-// Measured at 65,536 x 512: 4.76 ms (2-SM MMA), 5.06 ms (multicast), 5.42
-// ms (independent CTAs); clusters of 4 to 8 CTAs sharing rows by multicast
-// were slower still.  Every wait is bounded (pcc_ptx.cuh): a wait that runs
-// out records PCC_ERR_TIMEOUT and the CTA drains its copies, frees TMEM and
-// returns.
+// two halves of one super-tile, which need the same 256 B rows, as one 2-SM
+// MMA unit: each CTA loads its 128 A rows and 128 of the B rows into its own
+// stage, and the even CTA issues tcgen05.mma.cta_group::2 with M = 256; the
+// pair's tensor cores exchange the B halves, so each SM takes a third less
+// operand data from L2 than a CTA that loads all 256 B rows, and a stage is
+// a third smaller (six stages instead of four).  Both CTAs' copies count on
+// the even CTA's stage barrier; its commits release the stage in both CTAs
+// and hand each CTA its half of the accumulator; both epilogues release the
+// accumulator to the even CTA.  Otherwise (pcc_set_pair_mma(0), or K = 64
+// stages) every CTA runs its own M = 128 MMA over all 256 B rows.
+// Measured at 65,536 x 512: 4.76 ms (2-SM MMA), 5.42 ms (independent CTAs).
+// Every wait is bounded (pcc_ptx.cuh): a wait that runs out records
+// PCC_ERR_TIMEOUT; the CTA stops issuing, waits for every copy it (and, in
+// the pair form, its partner) issued, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -71,6 +66,7 @@
 #include "pcc_internal.h"
 #include "pcc_ptx.cuh"
 #include "pcc_sched.h"
+#include "tc_common.cuh"
 #include "tc_epilogue.cuh"
 
 namespace pcc {
@@ -95,8 +91,7 @@ struct TcParams {
   int64_t u_begin;   // units [u_begin, u_end)
   int64_t u_end;
   int nkb;           // K blocks of KB
-  int kalt;          // 1: the two halves of the K blocks go to two
-                     // accumulators (both TMEM buffers) for long rows
+  int nch;           // accumulator chunks per unit (tc_common.cuh)
   float out_scale;   // 2^-2s for FP16X3S, else 1
   float tau;
   const uint8_t* flags;
@@ -106,8 +101,9 @@ struct TcParams {
   uint64_t cap;
   int* status;
   uint64_t wait_ns;
-  int drop_loads;    // test hook: the producer issues no loads, so the
-                     // first operand wait runs out (pcc_debug_drop_loads)
+  int drop_loads;    // test hook (pcc_debug_drop_loads): 1 = no producer
+                     // issues loads, 2 / 3 = the odd / even CTA of each
+                     // pair issues none, so an operand wait runs out
 };
 
 // KB = K per ring stage: 64 (one 128-B swizzle row of 16-bit elements, 2
@@ -125,7 +121,7 @@ struct Cfg {
   static constexpr int kStages = (4 * 49152) / kStageBytes;
   static constexpr int kRingBytes = kStages * kStageBytes;
   static constexpr int kEpiBytes = kEpiWarps * 32 * kStagePad * 4;
-  static constexpr int kBarBytes = 256;
+  static constexpr int kBarBytes = 512;
   static constexpr int kSmemBytes = 1024 + kRingBytes + kEpiBytes + kBarBytes;
   static_assert(kSmemBytes <= 232448, "shared memory budget");
 };
@@ -150,8 +146,8 @@ __device__ __forceinline__ void unit_coords(BandCursor* cur, const TcParams& p,
   *col0 = xt * kTcSuper;
 }
 
-template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, int CL,
-          bool CROSS, bool PAIR>
+template <int NPROD, bool BF16, bool WRITE_R, bool EDGES, int KB, bool CROSS,
+          bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_tc(const __grid_constant__ CUtensorMap tm_hi,
                const __grid_constant__ CUtensorMap tm_lo,
@@ -160,11 +156,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   // B operand maps: the second matrix's for CROSS, else Z's own
   const CUtensorMap* mb_hi = CROSS ? &tmb_hi : &tm_hi;
   const CUtensorMap* mb_lo = CROSS ? &tmb_lo : &tm_lo;
-  static_assert(!PAIR || CL == 2, "the 2-SM MMA runs on CTA pairs");
+  static_assert(!PAIR || KB == 32, "the 2-SM MMA form uses K = 32 stages");
   using C = Cfg<NPROD, KB, PAIR>;
   constexpr int kTileA = C::kTileA;
   constexpr int kTileB = C::kTileB;
   constexpr int S = C::kStages;
+  static_assert(S <= 16, "fill log size");
   // PAIR: one instruction covers the pair's 256 rows
   constexpr uint32_t kIdesc = make_idesc_f16(BF16, PAIR ? 2 * kBM : kBM, kBN);
 
@@ -182,6 +179,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* mdone = tempty + 2;     // [1]
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  FillLog* flog = reinterpret_cast<FillLog*>(bars + 32);
+  static_assert(2 * S + 5 <= 31, "barrier area");
+  static_assert(32 * 8 + sizeof(FillLog) <= C::kBarBytes, "barrier area");
 
   auto sA_hi = [&](int s) { return ring + s * C::kStageBytes; };
   auto sB_hi = [&](int s) { return ring + s * C::kStageBytes + kTileA; };
@@ -198,8 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
-      // released by the MMA of every CTA (PAIR: by the one pair MMA)
-      mbar_init(&empty[s], PAIR ? 1 : CL);
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -208,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(mdone, 1);
     *abort_flag = 0;
+    fill_log_init(flog);
     fence_barrier_init();
   }
   if (warp == 0 && lane == 0) {
@@ -230,13 +230,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // barriers of both CTAs are initialised before any multicast lands
-  if constexpr (CL == 2) cluster_sync();
+  // both CTAs' barriers are initialised before the pair signals across them
+  if constexpr (PAIR) cluster_sync();
   const uint32_t tmem_base = *tmem_holder;
-  const uint32_t crank = CL == 2 ? cluster_ctarank() : 0u;
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
 
   WaitCtx w{abort_flag, p.status, p.wait_ns};
   const int64_t n = p.n;
+  const int nkb = p.nkb;
+  const int nch = p.nch;
 
   if (warp == 0) {
     // ------------------------------------------------------ TMA producer
@@ -245,19 +247,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       band_cursor_init(&cur, p.m, p.G);
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t issued_mask = 0;
-      uint32_t last_phase[S];
-      for (int s = 0; s < S; ++s) last_phase[s] = 0;
       const uint64_t pol = l2_policy_evict_last();
-      for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end && !p.drop_loads;
+      const bool drop = p.drop_loads == 1 ||
+                        (PAIR && p.drop_loads == 2 && crank == 1) ||
+                        (PAIR && p.drop_loads == 3 && crank == 0);
+      for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end && !drop;
            u += gridDim.x) {
         int64_t row0, col0;
         unit_coords<CROSS>(&cur, p, u, &row0, &col0);
-        // a cluster's CTAs run their units in lockstep (they share B), so
+        // the CTAs of a pair run their units in lockstep (they share B), so
         // only the single-CTA form skips units below the last row
-        if (CL == 1 && row0 >= n) continue;
+        if (!PAIR && row0 >= n) continue;
         bool ok = true;
-        for (int kb = 0; kb < p.nkb; ++kb) {
+        for (int kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, w)) {
             ok = false;
             break;
@@ -283,35 +285,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             // evict-first output stream
             tma_load_2d_hint(sA_hi(stage), &tm_hi, &full[stage], kc,
                              (int)row0, pol);
-            if constexpr (CL == 1) {
-              tma_load_2d_hint(sB_hi(stage), mb_hi, &full[stage], kc,
-                               (int)col0, pol);
-              tma_load_2d_hint(sB_hi(stage) + kTileA, mb_hi, &full[stage],
-                               kc, (int)col0 + kBM, pol);
-            } else {
-              // both CTAs need all 256 B rows: each loads its 128 and
-              // multicasts them to the pair
-              tma_load_2d_mc(sB_hi(stage) + crank * kTileA, mb_hi,
-                             &full[stage], kc, (int)(col0 + crank * kBM), 3,
-                             pol);
-            }
+            tma_load_2d_hint(sB_hi(stage), mb_hi, &full[stage], kc,
+                             (int)col0, pol);
+            tma_load_2d_hint(sB_hi(stage) + kTileA, mb_hi, &full[stage], kc,
+                             (int)col0 + kBM, pol);
             if (NPROD > 1) {
               tma_load_2d_hint(sA_lo(stage), &tm_lo, &full[stage], kc,
                                (int)row0, pol);
-              if constexpr (CL == 1) {
-                tma_load_2d_hint(sB_lo(stage), mb_lo, &full[stage], kc,
-                                 (int)col0, pol);
-                tma_load_2d_hint(sB_lo(stage) + kTileA, mb_lo, &full[stage],
-                                 kc, (int)col0 + kBM, pol);
-              } else {
-                tma_load_2d_mc(sB_lo(stage) + crank * kTileA, mb_lo,
-                               &full[stage], kc, (int)(col0 + crank * kBM), 3,
-                               pol);
-              }
+              tma_load_2d_hint(sB_lo(stage), mb_lo, &full[stage], kc,
+                               (int)col0, pol);
+              tma_load_2d_hint(sB_lo(stage) + kTileA, mb_lo, &full[stage],
+                               kc, (int)col0 + kBM, pol);
             }
           }
-          issued_mask |= 1u << stage;
-          last_phase[stage] = phase;
+          flog->fills[stage] += 1u;
+          flog->bytes[stage] = (uint32_t)C::kStageBytes;
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -319,14 +307,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
       }
-      // drain: every issued copy must land before the CTA may exit (PAIR:
-      // the even CTA's barriers also count the odd CTA's copies)
-      WaitCtx wd = w;
-      volatile int never = 0;
-      wd.abort_flag = &never;
-      if (!PAIR || crank == 0)
-        for (int s = 0; s < S; ++s)
-          if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------- MMA issuer
@@ -336,89 +316,72 @@ __global__ void __launch_bounds__(kThreads, 1)
       band_cursor_init(&cur, p.m, p.G);
       int stage = 0;
       uint32_t phase = 0;
+      // the accumulator buffer alternates with every chunk
       int acc = 0;
       uint32_t aphase = 0;
-      for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
+      bool ok = true;
+      for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end && ok;
+           u += gridDim.x) {
         int64_t row0, col0;
         unit_coords<CROSS>(&cur, p, u, &row0, &col0);
-        if (CL == 1 && row0 >= n) continue;
-        if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) break;
-        const int acc0 = acc;
-        uint32_t aph1 = aphase;
-        if (p.kalt) {
-          // a long-row unit also takes the other buffer of the ring, for
-          // the second half of its K blocks: that buffer is awaited only
-          // there, so the first half overlaps the previous unit's stores
-          acc ^= 1;
-          if (acc == 0) aphase ^= 1u;
-          aph1 = aphase;
-        }
-        tc_fence_after();
-        const uint32_t d_tmem0 = tmem_base + (uint32_t)(acc0 * kBN);
-        const uint32_t d_tmem1 = tmem_base + (uint32_t)(acc * kBN);
-        const int khalf = p.kalt ? p.nkb / 2 : p.nkb;
-        bool ok = true;
-        for (int kb = 0; kb < p.nkb; ++kb) {
-          if (p.kalt && kb == khalf) {
-            if (!mbar_wait(&tempty[acc], aph1 ^ 1u, w)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-          }
-          const uint32_t d_tmem = (p.kalt && kb >= khalf) ? d_tmem1 : d_tmem0;
-          const uint32_t first = kb == 0 || kb == khalf;
-          if (!mbar_wait(&full[stage], phase, w)) {
+        if (!PAIR && row0 >= n) continue;
+        for (int c = 0; c < nch && ok; ++c) {
+          if (!mbar_wait(&tempty[acc], aphase ^ 1u, w)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t aH = smem_u32(sA_hi(stage));
-          const uint32_t bH = smem_u32(sB_hi(stage));
-          const uint32_t aL = smem_u32(sA_lo(stage));
-          const uint32_t bL = smem_u32(sB_lo(stage));
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kBN);
+          const int kb0 = chunk_begin(nkb, nch, c);
+          const int kb1 = chunk_begin(nkb, nch, c + 1);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(&full[stage], phase, w)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t aH = smem_u32(sA_hi(stage));
+            const uint32_t bH = smem_u32(sB_hi(stage));
+            const uint32_t aL = smem_u32(sA_lo(stage));
+            const uint32_t bL = smem_u32(sB_lo(stage));
 #pragma unroll
-          for (int ks = 0; ks < KB / kUK; ++ks) {
-            const uint32_t off = ks * kUK * 2;  // bytes along K
-            const uint64_t dAH = kmajor_desc<C::kSwz>(aH + off);
-            const uint64_t dBH = kmajor_desc<C::kSwz>(bH + off);
-            auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
-              if constexpr (PAIR)
-                umma_f16_pair(d_tmem, a, b, kIdesc, acc_in);
-              else
-                umma_f16(d_tmem, a, b, kIdesc, acc_in);
-            };
-            mma(dAH, dBH, (first && ks == 0) ? 0u : 1u);
-            if (NPROD >= 3) {
-              const uint64_t dAL = kmajor_desc<C::kSwz>(aL + off);
-              const uint64_t dBL = kmajor_desc<C::kSwz>(bL + off);
-              mma(dAH, dBL, 1u);
-              mma(dAL, dBH, 1u);
-              if (NPROD == 4) mma(dAL, dBL, 1u);
+            for (int ks = 0; ks < KB / kUK; ++ks) {
+              const uint32_t off = ks * kUK * 2;  // bytes along K
+              const uint64_t dAH = kmajor_desc<C::kSwz>(aH + off);
+              const uint64_t dBH = kmajor_desc<C::kSwz>(bH + off);
+              auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
+                if constexpr (PAIR)
+                  umma_f16_pair(d_tmem, a, b, kIdesc, acc_in);
+                else
+                  umma_f16(d_tmem, a, b, kIdesc, acc_in);
+              };
+              mma(dAH, dBH, (kb == kb0 && ks == 0) ? 0u : 1u);
+              if (NPROD >= 3) {
+                const uint64_t dAL = kmajor_desc<C::kSwz>(aL + off);
+                const uint64_t dBL = kmajor_desc<C::kSwz>(bL + off);
+                mma(dAH, dBL, 1u);
+                mma(dAL, dBH, 1u);
+                if (NPROD == 4) mma(dAL, dBL, 1u);
+              }
+            }
+            if constexpr (PAIR)
+              umma_commit_pair(&empty[stage], 3);  // frees the stage in both
+            else
+              umma_commit(&empty[stage]);
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
             }
           }
+          if (!ok) break;
+          // PAIR: each CTA's epilogue reads its own half of the accumulator
           if constexpr (PAIR)
-            umma_commit_pair(&empty[stage], 3);  // frees the stage in both
-          else if constexpr (CL == 1)
-            umma_commit(&empty[stage]);
+            umma_commit_pair(&tfull[acc], 3);
           else
-            umma_commit_mc(&empty[stage], 3);  // frees the stage in both
-          if (++stage == S) {
-            stage = 0;
-            phase ^= 1u;
-          }
+            umma_commit(&tfull[acc]);
+          acc ^= 1;
+          if (acc == 0) aphase ^= 1u;
         }
-        if (!ok) break;
-        if constexpr (PAIR) {
-          // each CTA's epilogue reads its own half of the accumulator
-          umma_commit_pair(&tfull[acc0], 3);
-          if (p.kalt) umma_commit_pair(&tfull[acc], 3);
-        } else {
-          umma_commit(&tfull[acc0]);
-          if (p.kalt) umma_commit(&tfull[acc]);
-        }
-        acc ^= 1;
-        if (acc == 0) aphase ^= 1u;
       }
       // all MMAs issued by this thread complete before TMEM is released
       if constexpr (PAIR)
@@ -441,10 +404,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     band_cursor_init(&cur, p.m, p.G);
     int acc = 0;
     uint32_t aphase = 0;
+    const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
+    // release a TMEM buffer to the MMA issuer (PAIR: the even CTA's)
+    auto release = [&](int a) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR && crank != 0)
+          mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
+        else
+          mbar_arrive(&tempty[a]);
+      }
+    };
     for (int64_t u = p.u_begin + blockIdx.x; u < p.u_end; u += gridDim.x) {
       int64_t row0, col0;
       unit_coords<CROSS>(&cur, p, u, &row0, &col0);
-      if (CL == 1 && row0 >= n) continue;
+      if (!PAIR && row0 >= n) continue;
       const int64_t rbase = row0 + q * 32;  // first row of this warp
       const int64_t jw0 = col0 + h * 128;   // first column of this warp
       // flags do not depend on the accumulator: load them before waiting
@@ -456,67 +431,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t jj = jw0 + c * 32 + lane;
         cfl[c] = (jj < p.ncol) ? p.cflags[jj] : 1;
       }
+      // chunks: each finished chunk is added into the next one, whose
+      // buffer then holds the unit's running sum
+      int last = -1;
       bool ok = true;
-      const int acc0 = acc;
-      if (lane == 0) ok = mbar_wait(&tfull[acc], aphase, w);
-      if (p.kalt) {
+      for (int c = 0; c < nch; ++c) {
+        bool okw = true;
+        if (lane == 0) okw = mbar_wait(&tfull[acc], aphase, w);
+        if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (last >= 0) {
+          fold_acc(tmem_base + lane_off + (uint32_t)(last * kBN),
+                   tmem_base + lane_off + (uint32_t)(acc * kBN));
+          release(last);
+        }
+        last = acc;
         acc ^= 1;
         if (acc == 0) aphase ^= 1u;
-        if (lane == 0 && ok) ok = mbar_wait(&tfull[acc], aphase, w);
       }
-      if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
-      tc_fence_after();
+      if (!ok) break;
       const uint32_t rflags = __ballot_sync(0xffffffffu, rf != 0);
       // packed index of (rbase, 0); row i+1 starts n - i - 2 later (dense:
       // rbase * ldr, rows ldr apart)
       const int64_t base0 =
           (CROSS ? rbase * p.ldr : pair_row_base(n, rbase)) - p.r_off;
-      const uint32_t lane_off = ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
-      const uint32_t t_row = tmem_base + lane_off + (uint32_t)(acc0 * kBN);
       const EpiOut eo{p.R, p.out_scale, p.tau, p.edges, p.count, p.cap,
                       p.status};
-      // release a TMEM buffer to the MMA issuer (PAIR: the even CTA's)
-      auto release = [&](int a) {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if (PAIR && crank != 0)
-            mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
-          else
-            mbar_arrive(&tempty[a]);
-        }
-      };
-      uint32_t t_out = t_row;
-      if (p.kalt) {
-        // fold the first half's accumulator into the second's and free it
-        t_out = tmem_base + lane_off + (uint32_t)(acc * kBN);
-        fold_acc(t_row, t_out);
-        release(acc0);
-      }
-      epilogue_rows<WRITE_R, EDGES, CROSS>(t_out, stg, lane, n, rbase, jw0,
-                                           base0, rflags, cfl, eo, p.ncol,
-                                           p.ldr);
-      release(p.kalt ? acc : acc0);
-      acc ^= 1;
-      if (acc == 0) aphase ^= 1u;
+      epilogue_rows<WRITE_R, EDGES, CROSS>(
+          tmem_base + lane_off + (uint32_t)(last * kBN), stg, lane, n, rbase,
+          jw0, base0, rflags, cfl, eo, p.ncol, p.ldr);
+      release(last);
     }
   }
 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if constexpr (PAIR) {
-    // after an abort, the odd CTA's last copies are counted on barriers no
-    // one waits for any more: give them time to land (bounded, error path)
-    if (*abort_flag && threadIdx.x == 0) {
-      const uint64_t t0 = global_timer_ns();
-      while (global_timer_ns() - t0 < 200000u) {
-      }
-    }
-    __syncthreads();
-  }
-  // neither CTA leaves while the other may still write its shared memory
-  if constexpr (CL == 2) cluster_sync();
+  // every copy issued by this CTA (PAIR: by either CTA) has landed before
+  // a CTA of the cluster may exit
+  drain_ring<PAIR>(full, nullptr, flog, S, w, crank);
   if (warp == 1) {
     __syncwarp();
     if constexpr (PAIR)
@@ -534,49 +490,46 @@ cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
   const CUtensorMap& tbh = KB == 64 ? ZB->tm_hi : ZB->tm_hi32;
   const CUtensorMap& tbl = KB == 64 ? ZB->tm_lo : ZB->tm_lo32;
   const int64_t tiles = (p.u_end - p.u_begin) / 2;
-  if (tc_tuning().cluster == 2 && tiles >= 2) {
-    // the 2-SM MMA form exists for K = 32 stages
-    constexpr bool kPairOk = KB == 32;
-    const bool pair = kPairOk && tc_tuning().pair_mma != 0;
-    auto fn = pair ? k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2, CROSS,
-                                kPairOk>
-                   : k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 2, CROSS,
-                                false>;
-    const int smem = pair ? Cfg<NPROD, KB, kPairOk>::kSmemBytes
-                          : Cfg<NPROD, KB, false>::kSmemBytes;
-    cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    // per template instance, form and device
-    static int max_clusters_of[2][kDeviceSlots] = {};
-    int& max_clusters = max_clusters_of[pair ? 1 : 0][device_slot(Z->device)];
-    if (max_clusters == 0) {
-      cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
-      int mc = 0;
-      if (cudaOccupancyMaxActiveClusters(&mc, fn, &cfg) != cudaSuccess ||
-          mc <= 0) {
-        cudaGetLastError();
-        mc = num_sms(Z->device) / 2;
+  const TcTuning tn = tc_tuning();
+  if constexpr (KB == 32) {
+    if (tn.cluster == 2 && tn.pair_mma != 0 && tiles >= 2) {
+      auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, 32, CROSS, true>;
+      const int smem = Cfg<NPROD, 32, true>::kSmemBytes;
+      cudaError_t e =
+          ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.blockDim = dim3(kThreads, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      // per template instance and device
+      static int max_clusters_of[kDeviceSlots] = {};
+      int& max_clusters = max_clusters_of[device_slot(Z->device)];
+      if (max_clusters == 0) {
+        cfg.gridDim = dim3(2 * (unsigned)(num_sms(Z->device) / 2), 1, 1);
+        int mc = 0;
+        if (cudaOccupancyMaxActiveClusters(&mc, fn, &cfg) != cudaSuccess ||
+            mc <= 0) {
+          cudaGetLastError();
+          mc = num_sms(Z->device) / 2;
+        }
+        max_clusters = mc;
       }
-      max_clusters = mc;
+      int64_t ncl = tiles < max_clusters ? tiles : max_clusters;
+      cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
+      e = cudaLaunchKernelEx(&cfg, fn, th, tl, tbh, tbl, p);
+      if (e != cudaSuccess) return e;
+      return cudaGetLastError();
     }
-    int64_t ncl = tiles < max_clusters ? tiles : max_clusters;
-    cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
-    e = cudaLaunchKernelEx(&cfg, fn, th, tl, tbh, tbl, p);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
   }
-  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, 1, CROSS, false>;
+  auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, CROSS, false>;
   const int smem = Cfg<NPROD, KB, false>::kSmemBytes;
   cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
@@ -600,7 +553,7 @@ template <int KB, bool CROSS>
 cudaError_t launch_kb(const pcc_zmat* Z, const pcc_zmat* ZB, TcParams& p,
                       int grid, bool write_r, bool edges_on, cudaStream_t s) {
   p.nkb = (int)(Z->lpad / KB);
-  p.kalt = (Z->lpad > tc_tuning().kalt_min_l && p.nkb >= 2) ? 1 : 0;
+  p.nch = accum_chunks(Z->lpad, p.nkb);
   switch (Z->prec) {
     case PCC_PREC_BF16X3:
       return launch_prec<3, true, KB, CROSS>(Z, ZB, p, grid, write_r,
@@ -640,7 +593,7 @@ TcParams base_params(const pcc_zmat* Z, float* R, float tau,
   p.cap = cap;
   p.status = Z->status;
   p.wait_ns = wait_limit_ns();
-  p.drop_loads = debug_drop_loads() ? 1 : 0;
+  p.drop_loads = debug_drop_loads();
   return p;
 }
 

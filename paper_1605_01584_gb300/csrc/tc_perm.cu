@@ -38,6 +38,7 @@
 #include "pcc_internal.h"
 #include "pcc_ptx.cuh"
 #include "pcc_sched.h"
+#include "tc_common.cuh"
 
 namespace pcc {
 namespace {
@@ -112,7 +113,7 @@ struct PCfg {
   // stage: [B hi | B lo], streamed A in front of them
   static constexpr int kStageBytes =
       RESA ? 2 * kBHalf : 2 * kPTile + 2 * kBHalf;
-  static constexpr int kBarBytes = 256;
+  static constexpr int kBarBytes = 512;
   static constexpr int kStages =
       (kPSmemBudget - 1024 - kABytes - kBarBytes) / kStageBytes > 8
           ? 8
@@ -292,6 +293,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
   uint64_t* mdone = aempty + 1;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  // fills of the ring stages and (slot S) of the resident A tile
+  FillLog* flog = reinterpret_cast<FillLog*>(bars + 32);
+  static_assert(2 * S + 7 <= 31 && S + 1 <= 16, "barrier area");
+  static_assert(32 * 8 + sizeof(FillLog) <= C::kBarBytes, "barrier area");
 
   // stage layout: RESA: [B hi | B lo]; else [A hi | A lo | B hi | B lo];
   // B hi and lo hold 256 rows each: the first permutation's 128 rows, then
@@ -321,6 +326,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     mbar_init(aempty, 1);
     mbar_init(mdone, 1);
     *abort_flag = 0;
+    fill_log_init(flog);
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -380,11 +386,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
       const uint64_t pol = l2_policy_evict_last();
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t issued_mask = 0, last_phase[S];
-      for (int s = 0; s < S; ++s) last_phase[s] = 0;
       uint32_t aph = 0;
-      bool a_issued = false;
-      uint32_t a_last = 0;
       bool ok = true;
       for (int64_t it = wid; it < p.items && ok; it += wstride) {
         int64_t row0, col0;
@@ -393,8 +395,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
         if (klen <= 0) continue;
         if (RESA) {
           if (!mbar_wait(aempty, aph ^ 1u, w)) break;
-          a_issued = true;
-          a_last = aph;
+          flog->fills[S] += 1u;
+          flog->bytes[S] = (uint32_t)(p.nkb * 2 * kPTile);
           if constexpr (PAIR) {
             // both CTAs' A tiles count on the even CTA's barrier
             if (crank == 0)
@@ -481,23 +483,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
               }
             }
-            issued_mask |= 1u << stage;
-            last_phase[stage] = phase;
+            flog->fills[stage] += 1u;
+            flog->bytes[stage] =
+                PAIR ? (RESA ? 0u : 2u * kPTile) + 2u * kPTile : bytes;
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
             }
           }
         }
-      }
-      // drain (PAIR: the even CTA's barriers count both CTAs' copies)
-      WaitCtx wd = w;
-      volatile int never = 0;
-      wd.abort_flag = &never;
-      if (!PAIR || crank == 0) {
-        for (int s = 0; s < S; ++s)
-          if (issued_mask & (1u << s)) mbar_wait(&full[s], last_phase[s], wd);
-        if (RESA && a_issued) mbar_wait(afull, a_last, wd);
       }
     }
   } else if (warp == 1) {
@@ -672,18 +666,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if constexpr (PAIR) {
-    // after an abort, the odd CTA's last copies are counted on barriers no
-    // one waits for any more: give them time to land (bounded, error path)
-    if (*abort_flag && threadIdx.x == 0) {
-      const uint64_t t0 = global_timer_ns();
-      while (global_timer_ns() - t0 < 200000u) {
-      }
-    }
-    __syncthreads();
-    // neither CTA leaves while the other may still use its memory or TMEM
-    cluster_sync();
-  }
+  // every copy issued by this CTA (PAIR: by either CTA) has landed before
+  // a CTA of the pair may exit
+  drain_ring<PAIR>(full, RESA ? afull : nullptr, flog, S, w, crank);
   if (warp == 1) {
     __syncwarp();
     if constexpr (PAIR)

@@ -9,8 +9,15 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("cluster,pair", [(2, 1), (2, 0), (1, 0)])
-def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster, pair):
+@pytest.mark.parametrize("cluster,pair,drop", [(2, 1, 1), (1, 0, 1),
+                                               (2, 1, 2), (2, 1, 3)])
+def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster, pair,
+                                                  drop):
+    """drop 1: no CTA issues loads; 2 / 3: only the odd / even CTA of each
+    pair issues none, so the copies of the other one are in flight (or
+    landed) when the waits run out and the end-of-kernel drain must cancel
+    the missing share (2) or arm the unarmed one (3) before the CTAs
+    leave."""
     import torch
     pcc = pcc_gpu
     X = torch.from_numpy(synth.counts_log(1200, 64, 31)).cuda()
@@ -21,7 +28,7 @@ def test_wait_timeout_is_reported_and_recoverable(pcc_gpu, cluster, pair):
     pcc.pcc_set_tuning(cluster=cluster, pair_mma=pair)
     try:
         pcc.pcc_set_wait_limit_ns(200_000_000)  # 0.2 s
-        pcc.pcc_debug_drop_loads(True)
+        pcc.pcc_debug_drop_loads(drop)
         pcc.pcc_allpairs_upper(Z, R)
         assert pcc.pcc_sync_status(Z) == pcc.PCC_ERR_TIMEOUT
     finally:

@@ -1,13 +1,14 @@
-"""The CTA-pair forms of the tensor-core pair kernel give the same results.
+"""The CTA-pair form of the tensor-core pair kernel gives the same results
+as independent CTAs.
 
-With CTA pairs the tile's two 128-row halves either run one MMA each (the
-column rows reach both CTAs by TMA multicast) or one 2-SM MMA over both
-(tcgen05.mma.cta_group::2, M = 256; each CTA loads only its half of the
-column rows).  Each accumulator sees the same products in the same K order
-and the epilogue is shared, so the outputs must agree bit for bit: over
-every split form, ragged shapes, tile ranges, two accumulators for long
-rows, the fused edge list and the two-matrix form.  One case is also held
-against the FP64 oracle.
+A super-tile's two 128-row halves either run on two independent CTAs (one
+M = 128 MMA each, every CTA loading all 256 column rows) or on a CTA pair
+as one 2-SM MMA (tcgen05.mma.cta_group::2, M = 256; each CTA loads only its
+half of the column rows).  Each accumulator sees the same products in the
+same K order and the epilogue is shared, so the outputs must agree bit for
+bit: over every split form, ragged shapes, tile ranges, chunked
+accumulation of long rows, the fused edge list and the two-matrix form.
+One case is also held against the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -27,15 +28,16 @@ def _data(n, l, seed):
 
 
 class _Form:
-    """cluster 2, K = 32 stages, 2-SM MMA on or off; restores the knobs."""
+    """K = 32 stages; CTA pairs with the 2-SM MMA (pair = 1) or independent
+    CTAs (pair = 0); restores the knobs."""
 
     def __init__(self, pcc, pair, band=0):
         self.pcc, self.pair, self.band = pcc, pair, band
 
     def __enter__(self):
         self.old = self.pcc.pcc_get_tuning()
-        self.pcc.pcc_set_tuning(stage_k=32, cluster=2, band_rows=self.band,
-                                pair_mma=self.pair)
+        self.pcc.pcc_set_tuning(stage_k=32, cluster=2 if self.pair else 1,
+                                band_rows=self.band, pair_mma=self.pair)
 
     def __exit__(self, *a):
         o = self.old
@@ -64,7 +66,7 @@ def _same_bits(a, b, what):
 
 @pytest.mark.parametrize("prec", ["fp16x3s", "bf16x3", "bf16x4", "bf16x1"])
 @pytest.mark.parametrize("n,l", [(300, 40), (1000, 130), (2300, 96)])
-def test_pair_mma_equals_multicast_bits(pcc_gpu, prec, n, l):
+def test_pair_mma_equals_single_cta_bits(pcc_gpu, prec, n, l):
     import torch
     pcc = pcc_gpu
     X = torch.from_numpy(_data(n, l, 80 + n + l)).cuda()
@@ -97,7 +99,8 @@ def test_pair_mma_tile_ranges(pcc_gpu):
 
 
 def test_pair_mma_two_accumulators_and_oracle(pcc_gpu):
-    """l > 1024: K blocks alternate between two accumulators."""
+    """l > 1024: each unit accumulates in two chunks, folded by the
+    epilogue."""
     import torch
     pcc = pcc_gpu
     n, l = 700, 1100

@@ -94,20 +94,87 @@ def test_fp64_modules_config(pcc_gpu):
     compare(got, want, 1e-12, "fp64 2000x128")
 
 
-@pytest.mark.parametrize("n,l,prec", [
-    (300, 1500, "fp16x3s"),   # two accumulators (l > 1,024)
-    (300, 1500, "bf16x3"),
-    (257, 2049, "auto"),      # AUTO switches to BF16X3 above 2,048
-    (300, 5000, "auto"),      # the paper's row length
+@pytest.mark.parametrize("n,l,prec,tol", [
+    (300, 1500, "fp16x3s", 1e-5),   # 3 accumulator chunks (l > 1,024)
+    (300, 1500, "bf16x3", 1e-5),
+    (257, 2049, "auto", 1e-5),
+    (300, 5000, "auto", 1e-5),      # the paper's row length
+    # count data shaped like the paper's human dataset (l = 5,072), with
+    # planted modules: the default form with a 2x margin on 1e-5
+    (640, 5072, "auto", 5e-6),
 ])
-def test_long_rows_parity(pcc_gpu, n, l, prec):
-    """Rows past 1,024 samples (the K blocks split over two TMEM
-    accumulators, folded before the stores) against the oracle, with
-    planted modules (r -> 1), a constant row and a 1e5 offset row."""
+def test_long_rows_parity(pcc_gpu, n, l, prec, tol):
+    """Rows past 1,024 samples (each unit accumulated in chunks of at most
+    640 samples, every chunk added into the next before the stores)
+    against the oracle, with planted modules (r -> 1), a constant row and a
+    1e5 offset row."""
     X = _data(n, l, seed=3000 + n + l)
     got, _ = gpu_allpairs(pcc_gpu, X, prec)
     want = oracle.pcc_upper(X)
-    compare(got, want, 1e-5, f"{prec} n={n} l={l}")
+    err = compare(got, want, tol, f"{prec} n={n} l={l}")
+    print(f"{prec} n={n} l={l}: max|dr| {err:.2e}")
+
+
+class _Knobs:
+    """Sets band rows and the CTA-pair form for the block; restores them."""
+
+    def __init__(self, pcc, band, pair):
+        self.pcc, self.band, self.pair = pcc, band, pair
+
+    def __enter__(self):
+        self.old = self.pcc.pcc_get_tuning()
+        self.pcc.pcc_set_tuning(band_rows=self.band,
+                                cluster=2 if self.pair else 1,
+                                pair_mma=self.pair)
+
+    def __exit__(self, *a):
+        o = self.old
+        self.pcc.pcc_set_tuning(o["stage_k"], o["cluster"], o["band_rows"],
+                                pair_mma=o["pair_mma"])
+
+
+@pytest.mark.parametrize("n,l", [(4500, 64), (4100, 1100), (4100, 1950)])
+@pytest.mark.parametrize("band,pair", [(1, 1), (2, 0)])
+def test_steady_state_parity(pcc_gpu, n, l, band, pair):
+    """Shapes large enough for the persistent loop's steady state: several
+    units per CTA (or CTA pair), many band transitions (one or two
+    super-tile rows per band), accumulator buffers reused unit after unit,
+    and 2 and 4 accumulator chunks per unit in sequence; every pair
+    against the oracle."""
+    X = _data(n, l, seed=4000 + n + l)
+    with _Knobs(pcc_gpu, band, pair):
+        got, Z = gpu_allpairs(pcc_gpu, X, "fp16x3s")
+        T = Z.num_tiles()
+    # more tiles than workers: each CTA (pair) walks several of them
+    assert T > 152
+    want = oracle.pcc_upper(X)
+    err = compare(got, want, 1e-5, f"n={n} l={l} band={band} pair={pair}")
+    print(f"n={n} l={l} band={band} pair={pair}: max|dr| {err:.2e}")
+
+
+@pytest.mark.parametrize("prec", ["fp16x3s", "bf16x3", "fp32", "fp64"])
+def test_near_constant_rows(pcc_gpu, prec):
+    """Rows whose mean dwarfs their spread (FP32 input): the row statistics
+    must not cancel.  1e7 + N(0, 1e-3) rounds to a constant in FP32 (ulp 1)
+    and must be flagged exactly as the oracle's 0/0; 1e4 + N(0, 1e-2) and
+    1e6 + N(0, 1) keep a spread of a few FP32 ulps and must match the
+    oracle's r; a pair of them is planted as exact affine copies."""
+    rng = np.random.default_rng(77)
+    n, l = 200, 300
+    X = synth.counts_log(n, l, 78, dtype=np.float32)
+    base4 = (1e4 + rng.normal(0, 1e-2, l)).astype(np.float32)
+    for k in range(10):
+        X[k] = (1e7 + rng.normal(0, 1e-3, l)).astype(np.float32)
+        X[10 + k] = (1e4 + rng.normal(0, 1e-2, l)).astype(np.float32)
+        X[20 + k] = (1e6 + rng.normal(0, 1.0, l)).astype(np.float32)
+    X[30] = base4
+    X[31] = base4 + np.float32(2.0)  # exact in FP32: r = 1
+    Xin = X.astype(np.float64) if prec == "fp64" else X
+    got, _ = gpu_allpairs(pcc_gpu, Xin, prec)
+    want = oracle.pcc_upper(Xin)
+    assert np.isnan(want[pcc_gpu.pcc_pair_index(n, 0, 50)])  # flagged row
+    assert not np.isnan(want[pcc_gpu.pcc_pair_index(n, 10, 50)])
+    compare(got, want, TOL[prec], f"{prec} near-constant rows")
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp16x3s"])

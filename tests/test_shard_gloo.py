@@ -141,3 +141,99 @@ def test_bench_times_are_the_max_over_ranks():
         p.join(timeout=120)
         assert p.exitcode == 0
     assert res == {0: 5.75, 1: 5.75}
+
+
+def _tc_rank_main(rank, world, port, n, l, band, path, out_q):
+    """One rank of the tensor-core schedule (banded 256 x 256 super-tiles):
+    its tile range's pairs, listed by the library's host schedule, computed
+    by the oracle into a packed array of its own (sentinel elsewhere), then
+    assembled by shard.gather_upper and shard.write_upper_shard."""
+    import torch.distributed as dist
+
+    import oracle
+    import paper_1605_01584_gb300 as pcc
+    import synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        pcc.load()
+        pcc.pcc_set_tuning(band_rows=band)  # host knob: no device needed
+        X = synth.counts_log(n, l, 17)
+        T = pcc.pcc_schedule_num_tiles(n, "fp16x3s")
+        b, e = shard.tile_range(rank, world, T)
+        I, J = [], []
+        for t in range(b, e):
+            r0, r1, c0, c1 = pcc.pcc_schedule_tile_rect(n, "fp16x3s", t)
+            for i in range(r0, r1):
+                js = np.arange(max(c0, i + 1), c1)
+                I.append(np.full(js.size, i))
+                J.append(js)
+        I = np.concatenate(I).astype(np.int64)
+        J = np.concatenate(J).astype(np.int64)
+        R = np.full(n * (n - 1) // 2, 7.0)
+        R[I * (2 * n - I - 1) // 2 + (J - I - 1)] = oracle.pcc_pairs(X, I, J)
+        whole = shard.gather_upper(R, n, "fp16x3s", rank, world, dist)
+        shard.write_upper_shard(path, R, n, "fp16x3s", rank, world)
+        dist.barrier()
+        if rank == 0:
+            out_q.put((T, whole, np.fromfile(path, dtype=np.float64)))
+        else:
+            assert whole is None
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_gather_through_tensor_core_schedule(tmp_path):
+    """Section III-D's ranges over the tensor-core kernels' banded
+    super-tile order: the host gather and the shared file each rebuild the
+    whole packed triangle, equal to the oracle's one-process result."""
+    import multiprocessing as mp
+
+    import oracle
+    import synth
+    n, l, band = 1300, 20, 2  # 6 x 6 super-tiles in 3 bands, 21 tiles
+    path = str(tmp_path / "upper.f64")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_tc_rank_main,
+                         args=(r, 2, port, n, l, band, path, q))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    T, whole, filed = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert T == 21
+    want = oracle.pcc_upper(synth.counts_log(n, l, 17))
+    for got in (whole, filed):
+        assert not np.any(got == 7.0)
+        assert np.array_equal(np.isnan(got), np.isnan(want))
+        ok = ~np.isnan(want)
+        assert np.array_equal(got[ok], want[ok])
+
+
+def test_schedule_rectangles_cover_each_pair_once():
+    """The host schedule's tiles cover every pair i < j exactly once, for
+    the tensor-core order at several band heights and the CUDA-core
+    order."""
+    import paper_1605_01584_gb300 as pcc
+    pcc.load()
+    before = pcc.pcc_get_tuning()
+    try:
+        for n, prec, band in [(700, "fp16x3s", 1), (1100, "bf16x3", 3),
+                              (1100, "auto", 32), (300, "fp32", 32),
+                              (200, "fp64", 32)]:
+            pcc.pcc_set_tuning(band_rows=band)
+            T = pcc.pcc_schedule_num_tiles(n, prec)
+            starts, lens = shard.tile_runs(n, prec, 0, T)
+            idx = shard._run_index(starts, lens)
+            assert np.array_equal(np.sort(idx), np.arange(n * (n - 1) // 2))
+            parts = [shard.tile_runs(n, prec, *shard.tile_range(r, 3, T))
+                     for r in range(3)]
+            cat = np.concatenate([shard._run_index(*p) for p in parts])
+            assert np.array_equal(cat, idx)
+    finally:
+        pcc.pcc_set_tuning(band_rows=before["band_rows"])
