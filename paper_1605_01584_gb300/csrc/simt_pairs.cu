@@ -71,7 +71,9 @@ struct SimtCross {
 
 template <typename T, typename OutT, int BT, int TT, int BK, bool WRITE_R,
           bool EDGES, bool CROSS>
-__global__ void __launch_bounds__(256)
+// FP32: two blocks per SM (at one, with 129 registers, the eight warps of a
+// block idle together at every stage barrier); FP64: three
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
     k_pairs_simt(const T* __restrict__ Z, const uint8_t* __restrict__ flags,
                  int64_t n, int64_t lpad, int64_t m, int64_t t0,
                  OutT* __restrict__ R, float tau, pcc_edge* __restrict__ edges,
@@ -88,8 +90,13 @@ __global__ void __launch_bounds__(256)
   constexpr int NV = BT * BK / 256 / VW;  // vector loads per thread/operand
   using VH = typename VecH<T, H>::type;
 
-  __shared__ __align__(16) T As[2][BK][BT + PAD];
-  __shared__ __align__(16) T Bs[2][BK][BT + PAD];
+  // operand stages; after the K loop the same memory stages the tile for
+  // the stores, half of its rows at a time
+  __shared__ __align__(16) T smem_ops[4 * BK * (BT + PAD)];
+  static_assert(BT / 2 <= 4 * BK, "a half tile fits the operand stages");
+  auto As = reinterpret_cast<T(*)[BK][BT + PAD]>(smem_ops);
+  auto Bs = reinterpret_cast<T(*)[BK][BT + PAD]>(smem_ops +
+                                                  2 * BK * (BT + PAD));
   __shared__ uint8_t fr[BT], fc[BT];
 
   const int tid = threadIdx.x;
@@ -182,43 +189,68 @@ __global__ void __launch_bounds__(256)
     }
   }
 
-  const int lane = tid & 31;
+  // Stores: each half of the tile's rows goes through shared memory, so
+  // that a warp writes 32 consecutive pairs of one row per instruction (a
+  // packed row's pairs are contiguous; thread blocks of 8 x 8 in registers
+  // would touch 16 sectors per store instruction).
+  const int lane = tid & 31, warp = tid >> 5;
+  T(*tile)[BT + PAD] = reinterpret_cast<T(*)[BT + PAD]>(smem_ops);
 #pragma unroll
-  for (int a = 0; a < TT; ++a) {
-    const int li = a < H ? ty * H + a : BT / 2 + ty * H + (a - H);
-    const int64_t i = row0 + li;
-    const int64_t base =
-        (CROSS ? i * cx.ldr : pair_row_base(n, i)) - cx.r_off;
+  for (int half = 0; half < 2; ++half) {
+    __syncthreads();  // operand stages (or the previous half) are free
 #pragma unroll
-    for (int b = 0; b < TT; ++b) {
-      const int lj = b < H ? tx * H + b : BT / 2 + tx * H + (b - H);
-      const int64_t j = col0 + lj;
-      const bool valid = (i < n) && (j < nb) && (CROSS || j > i);
-      const bool flagged = (fr[li] | fc[lj]) != 0;
-      T v = acc[a][b];
-      v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
-      if (flagged) v = T(NAN);
-      if constexpr (WRITE_R) {
-        if (valid) R[base + j] = (OutT)v;
+    for (int a = 0; a < H; ++a) {
+      const int li = ty * H + a;  // row within the half
+      const T* q = acc[half * H + a];
+      VH v0, v1;
+      if constexpr (H == 4) {
+        v0 = make_float4(q[0], q[1], q[2], q[3]);
+        v1 = make_float4(q[4], q[5], q[6], q[7]);
+      } else {
+        v0 = make_double2(q[0], q[1]);
+        v1 = make_double2(q[2], q[3]);
       }
-      if constexpr (EDGES) {
-        const bool e = valid && !flagged && fabs((double)v) >= (double)tau;
-        const unsigned mask = __ballot_sync(0xffffffffu, e);
-        if (mask) {
-          const int leader = __ffs(mask) - 1;
-          unsigned long long basei = 0;
-          if (lane == leader)
-            basei = atomicAdd(count, (unsigned long long)__popc(mask));
-          basei = __shfl_sync(0xffffffffu, basei, leader);
-          if (e) {
-            const unsigned long long idx =
-                basei + __popc(mask & ((1u << lane) - 1u));
-            if (idx < cap) {
-              edges[idx].i = (uint32_t)i;
-              edges[idx].j = (uint32_t)j;
-              edges[idx].r = (float)v;
-            } else {
-              atomicCAS(status, 0, (int)PCC_ERR_CAPACITY);
+      *reinterpret_cast<VH*>(&tile[li][tx * H]) = v0;
+      *reinterpret_cast<VH*>(&tile[li][BT / 2 + tx * H]) = v1;
+    }
+    __syncthreads();
+    for (int li = warp; li < BT / 2; li += 8) {
+      const int ri = half * (BT / 2) + li;  // row within the tile
+      const int64_t i = row0 + ri;
+      if (i >= n) break;
+      const int64_t base =
+          (CROSS ? i * cx.ldr : pair_row_base(n, i)) - cx.r_off;
+#pragma unroll
+      for (int c = 0; c < BT / 32; ++c) {
+        const int lj = c * 32 + lane;
+        const int64_t j = col0 + lj;
+        const bool valid = (j < nb) && (CROSS || j > i);
+        const bool flagged = (fr[ri] | fc[lj]) != 0;
+        T v = tile[li][lj];
+        v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
+        if (flagged) v = T(NAN);
+        if constexpr (WRITE_R) {
+          if (valid) R[base + j] = (OutT)v;
+        }
+        if constexpr (EDGES) {
+          const bool e = valid && !flagged && fabs((double)v) >= (double)tau;
+          const unsigned mask = __ballot_sync(0xffffffffu, e);
+          if (mask) {
+            const int leader = __ffs(mask) - 1;
+            unsigned long long basei = 0;
+            if (lane == leader)
+              basei = atomicAdd(count, (unsigned long long)__popc(mask));
+            basei = __shfl_sync(0xffffffffu, basei, leader);
+            if (e) {
+              const unsigned long long idx =
+                  basei + __popc(mask & ((1u << lane) - 1u));
+              if (idx < cap) {
+                edges[idx].i = (uint32_t)i;
+                edges[idx].j = (uint32_t)j;
+                edges[idx].r = (float)v;
+              } else {
+                atomicCAS(status, 0, (int)PCC_ERR_CAPACITY);
+              }
             }
           }
         }
