@@ -504,7 +504,8 @@ def run_gpu(args):
                 Rh.copy_(R, non_blocking=True)
             return pcc.pcc_edges_copy_host(E, cnt, EDGE_CAP, Eh)
 
-        e2e_step()
+        for _ in range(args.warmup):
+            e2e_step()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -528,6 +529,8 @@ def run_gpu(args):
                       "ms_per_step_median": statistics.median(walls),
                       "ms_per_step_min": min(walls),
                       "ms_per_step_max": max(walls),
+                      "ms_each_step": [round(w, 3) for w in walls],
+                      "warmup": args.warmup,
                       "steps": e2e_steps,
                       "api": "pcc_standardize_host + "
                              "pcc_threshold_edges_host + "
@@ -665,12 +668,23 @@ def run_batched(args):
         Rs.append(torch.empty(n * (n - 1) // 2, device="cuda"))
     gen_s = time.time() - t0
     stream = torch.cuda.current_stream()
+    tune_s = None
+    if args.tune:
+        # tune every shape bucket of the batch (K = 32, CTA pairs or single
+        # CTAs, band heights) into the tune cache before the timed steps
+        from paper_1605_01584_gb300 import autotune
+        t0 = time.time()
+        autotune.tune_batched([(n, l) for n, l in shapes], args.prec)
+        tune_s = time.time() - t0
+    # per-matrix (CTA form, band rows): the tune cache's best where it has
+    # an entry, else the current knobs; resolved once, reused every step
+    choices = pcc.pcc_allpairs_upper_batched(Zs, Rs)
 
     def step():
         # every matrix's standardize in one launch, then every matrix's
-        # pairs in one launch
+        # pairs in one persistent launch per CTA form
         pcc.pcc_standardize_batched(Xs, args.prec, Zs=Zs)
-        pcc.pcc_allpairs_upper_batched(Zs, Rs)
+        pcc.pcc_allpairs_upper_batched(Zs, Rs, choices=choices)
 
     ms_stream = _timed(step, max(3, min(args.steps, 10)), args.warmup, stream)
     # the whole step (one standardize launch per form, one pair launch) as
@@ -679,7 +693,7 @@ def run_batched(args):
     ms = ms_graph if ms_graph is not None else ms_stream
 
     def kern():
-        pcc.pcc_allpairs_upper_batched(Zs, Rs)
+        pcc.pcc_allpairs_upper_batched(Zs, Rs, choices=choices)
 
     ms_k = _timed(kern, max(3, min(args.steps, 10)), 1, stream)
     st = pcc.pcc_sync_status(Zs[0])
@@ -701,7 +715,15 @@ def run_batched(args):
            "ms_batched_kernel": ms_k, "status": st,
            "config": {"workload": f"{len(shapes)} uneven matrices "
                       "n~U{500..20000}, l~U{32..2048}", "split": args.prec,
-                      "matrices": len(shapes), "gen_seconds": gen_s},
+                      "matrices": len(shapes), "gen_seconds": gen_s,
+                      "tuned": bool(args.tune), "tune_seconds": tune_s},
+           "choices": {
+               "per_matrix": [{"n": n, "l": l, "pair": c[0], "band_rows":
+                               c[1]} for (n, l), c in zip(shapes, choices)],
+               "pair_form_matrices": sum(c[0] for c in choices),
+               "single_cta_matrices": sum(1 - c[0] for c in choices),
+               "launches": (1 if all(c[0] for c in choices) or
+                            not any(c[0] for c in choices) else 2)},
            "roofline": {"bound": "hbm", "achieved": out_bytes / (ms_k / 1e3)
                         / 1e9, "peak": hbm, "unit": "GB/s",
                         "frac": out_bytes / (ms_k / 1e3) / 1e9 / hbm,
@@ -869,6 +891,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_GENES)
     ap.add_argument("--matrices", type=int, default=64,
                     help="matrices of the batched workload (its first K)")
+    ap.add_argument("--tune", action="store_true",
+                    help="batched workload: tune each shape bucket first")
     ap.add_argument("--P", type=int, default=1000,
                     help="permutations of the perm workload")
     ap.add_argument("--l", type=int, default=L_SAMPLES)

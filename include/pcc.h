@@ -318,6 +318,27 @@ pcc_status pcc_perm_test(const pcc_zmat *Z, const int32_t *d_perms,
 pcc_status pcc_allpairs_upper_batched(const pcc_zmat *const *Zs, int32_t B,
                                       float *const *Rs, void *stream);
 
+/* pcc_allpairs_upper_batched with a choice per matrix (the tuner's, for
+ * each matrix's shape; the paper has no counterpart):
+ *   pair[b]       1: matrix b runs on CTA pairs as 2-SM MMAs, 0: on single
+ *                 CTAs (NULL: the current pcc_set_pair_mma / cluster knob
+ *                 for every matrix);
+ *   band_rows[b]  super-tile rows per band of matrix b's order, 1..4096
+ *                 (NULL: the current band_rows for every matrix).
+ * One kernel issues either 2-SM or 1-SM MMAs, so the matrices of each form
+ * run in one persistent launch of their own: one launch when all share a
+ * form, two (pair form first, both on `stream`) otherwise.  Each matrix's
+ * result has the bits of a pcc_allpairs_upper of it under the same form and
+ * band rows.  The work list is built and cached as in
+ * pcc_allpairs_upper_batched (per set of Zs, Rs and choices).
+ * Errors: as pcc_allpairs_upper_batched, and PCC_ERR_INVALID_ARG for a pair
+ * value other than 0 or 1 or a band_rows value out of range. */
+pcc_status pcc_allpairs_upper_batched_tuned(const pcc_zmat *const *Zs,
+                                            int32_t B, float *const *Rs,
+                                            const int32_t *pair,
+                                            const int32_t *band_rows,
+                                            void *stream);
+
 /* All pairs without any device allocation (the paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory,
  * e.g. code running inside another framework's memory pool, programs with
@@ -356,8 +377,10 @@ pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
  * (paper_1605_01584_gb300/autotune.py); they affect later launches only and
  * never the result.  0 (or <= 0 for the costs) keeps a value.
  *   stage_k    K per shared-memory ring stage: 32 (4 stages; 6 in the 2-SM
- *              pair form, whose stages are a third smaller) or 64 (2;
- *              independent CTAs only).
+ *              pair form, whose stages are a third smaller) or 64 (2; 3 in
+ *              the pair form; the default, PCC_TC_BK=32 in the environment
+ *              selects 32 when the library loads).  The batched and
+ *              permutation kernels always use K = 32.
  *   cluster    2 = CTA pairs running one 2-SM MMA (while
  *              pcc_set_pair_mma is on), 1 = independent CTAs.
  *   band_rows  super-tile rows per band of the pair schedule (rows of a
@@ -376,7 +399,7 @@ pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
  * each loading only half of the column operand, which the pair's tensor
  * cores exchange.  on = 0: independent CTAs, each loading its whole
  * operands.  No form copies an operand to several CTAs (no TMA multicast).
- *   pcc_allpairs_upper / _edges / cross (cluster = 2, stage_k = 32): the
+ *   pcc_allpairs_upper / _edges / cross (cluster = 2): the
  *   pair computes one 256 x 256 super-tile; on = 0: each CTA computes a
  *   128 x 256 half on its own.
  *   pcc_perm_test: the pair computes two 128 x 128 tiles of one tile

@@ -109,6 +109,8 @@ def load(path: str | None = None):
                                            _P, _I64, _SINK, _P, _P]),
         "pcc_perm_test": (_ST, [_P, _P, _I32, _I32, _I32, _P, _P]),
         "pcc_allpairs_upper_batched": (_ST, [_P, _I32, _P, _P]),
+        "pcc_allpairs_upper_batched_tuned": (_ST, [_P, _I32, _P, _P, _P,
+                                                   _P]),
         "pcc_sync_status": (_ST, [_P, _P]),
         "pcc_allpairs_upper_noalloc": (_ST, [_P, _I64, _I64, _I64, _I32, _P,
                                              _P, _P]),
@@ -439,12 +441,49 @@ def pcc_perm_test(Z: Zmat, d_perms, P: int, k0: int, k1: int, d_counts,
            "pcc_perm_test")
 
 
-def pcc_allpairs_upper_batched(Zs, Rs, stream=None):
+_FORM_NAMES = {PCC_PREC_BF16X3: "bf16x3", PCC_PREC_FP16X3S: "fp16x3s",
+               PCC_PREC_BF16X4: "bf16x4", PCC_PREC_BF16X1: "bf16x1"}
+
+
+def pcc_allpairs_upper_batched(Zs, Rs, stream=None, choices="auto",
+                               cache=None):
+    """All pairs of many standardized matrices (pcc.h).  choices:
+      "auto"  (default) each matrix gets the tuner's best CTA form and band
+              rows for its shape when the tune cache (autotune.cache_path()
+              or `cache`, a path or a loaded dict) has an entry for it; the
+              others run under the current knobs;
+      None    every matrix under the current knobs;
+      a list  (pair, band_rows) per matrix.
+    Returns the list of (pair, band_rows) used per matrix."""
     B = len(Zs)
     harr = (ctypes.c_void_p * B)(*[z.handle.value for z in Zs])
     rarr = (ctypes.c_void_p * B)(*[r.data_ptr() for r in Rs])
-    _check(load().pcc_allpairs_upper_batched(harr, B, rarr, _stream(stream)),
-           "pcc_allpairs_upper_batched")
+    t = pcc_get_tuning()
+    default = (1 if t["pair_mma"] and t["cluster"] == 2 else 0,
+               t["band_rows"])
+    if choices is None:
+        used = [default] * B
+    elif isinstance(choices, str) and choices == "auto":
+        from . import autotune
+        c = autotune.load_cache(cache) if cache is None or \
+            isinstance(cache, str) else cache
+        used = []
+        for z in Zs:
+            info = z.info()
+            form = _FORM_NAMES.get(info["prec"])  # others: rejected below
+            b = None if form is None else autotune.lookup_batched(
+                info["n"], info["l"], form, c)
+            used.append(b if b is not None else default)
+    else:
+        used = [(int(p), int(g)) for p, g in choices]
+        if len(used) != B:
+            raise ValueError("one (pair, band_rows) per matrix")
+    pa = (_I32 * B)(*[u[0] for u in used])
+    ga = (_I32 * B)(*[u[1] for u in used])
+    _check(load().pcc_allpairs_upper_batched_tuned(harr, B, rarr, pa, ga,
+                                                   _stream(stream)),
+           "pcc_allpairs_upper_batched_tuned")
+    return used
 
 
 def pcc_allpairs_upper_noalloc(X, R, prec="auto", d_status=None,

@@ -2,9 +2,9 @@
 
 The knobs never change results, only speed:
   stage_k    K per shared-memory ring stage (32: 4 stages, 6 in the 2-SM
-             pair form; 64: 2 stages, independent CTAs only)
+             pair form; 64: 2 stages, 3 in the pair form)
   pair_mma   1 = CTA pairs running one 2-SM MMA (each CTA loads half of
-             the column operand; stage_k 32), 0 = independent CTAs; the
+             the column operand), 0 = independent CTAs; the
              cluster knob follows it (2 with pairs, 1 without)
   band_rows  super-tile rows per band of the pair schedule
 and the batched work split's cost model (cycles per unit c0, per K block and
@@ -99,6 +99,51 @@ def lookup(n: int, l: int, prec: str, cache: dict | None = None):
     return best
 
 
+def lookup_batched(n: int, l: int, prec: str, cache: dict | None = None):
+    """(pair, band_rows) for one matrix of a batched launch: the fastest
+    timed candidate with K = 32 stages (the batched kernel's) in the entry
+    lookup() would use; None without one."""
+    cache = load_cache() if cache is None else cache
+    key = bucket(n, l, prec)
+    entry = cache.get(key) if _usable(cache.get(key)) else None
+    if entry is None:
+        lp = (l + 63) // 64 * 64
+        dist = None
+        for k, v in cache.items():
+            if not k.endswith(f"_l{lp}_{prec}") or not _usable(v):
+                continue
+            d = abs(math.log2(int(k.split("_")[0][1:])) -
+                    math.log2(max(n, 2)))
+            if dist is None or d < dist:
+                entry, dist = v, d
+    if entry is None:
+        return None
+    runs = [r for r in entry.get("all", []) if isinstance(r, dict) and
+            r.get("stage_k") == 32 and isinstance(r.get("ms"), (int, float))]
+    if not runs:
+        return None
+    b = min(runs, key=lambda r: r["ms"])
+    return (1 if b.get("pair_mma") else 0, int(b["band_rows"]))
+
+
+def tune_batched(shapes, prec: str = "auto", reps: int = 3,
+                 bands=(8, 16, 32), path: str | None = None) -> dict:
+    """Tune every distinct shape bucket of a batch (K = 32 stages, CTA pairs
+    or single CTAs, the given band heights) on a synthetic matrix of the
+    first shape of that bucket, and cache the results; returns bucket ->
+    entry."""
+    done = {}
+    for n, l in shapes:
+        key = bucket(n, l, "?")[:-2]
+        if key in done:
+            continue
+        done[key] = tune_pairs(n, l, prec, reps=reps, path=path,
+                               candidates={"stage_k": (32,),
+                                           "pair_mma": (1, 0),
+                                           "band_rows": tuple(bands)})
+    return done
+
+
 def apply(n: int, l: int, prec: str, cache: dict | None = None) -> bool:
     """Set the library's knobs to the best known values for this shape;
     False (nothing changed) if the cache has no entry for it."""
@@ -145,9 +190,6 @@ def tune_pairs(n: int, l: int, prec: str = "auto", candidates=None,
     try:
         for sk, pm, bd in itertools.product(
                 cand["stage_k"], cand["pair_mma"], cand["band_rows"]):
-            # the 2-SM pair form runs with K = 32 stages only
-            if pm and sk != 32:
-                continue
             cl = 2 if pm else 1
             pcc_set_tuning(stage_k=sk, cluster=cl, band_rows=bd, pair_mma=pm)
             ms = _time_ms(lambda: pcc_allpairs_upper(Z, R), reps)

@@ -102,7 +102,9 @@ std::mutex g_tune_mu;
 TcTuning g_tune = [] {
   TcTuning t;
   const char* e = getenv("PCC_TC_BK");
-  t.stage_k = (e && atoi(e) == 64) ? 64 : 32;
+  // K = 64 stages: 3-4% faster than K = 32 in the 2-SM pair form at
+  // 65,536 x 512 (fewer, larger copies and stage hand-offs per MMA work)
+  t.stage_k = (e && atoi(e) == 32) ? 32 : 64;
   e = getenv("PCC_TC_CLUSTER");
   t.cluster = (e && atoi(e) == 1) ? 1 : 2;
   e = getenv("PCC_TC_PAIR");
@@ -122,12 +124,13 @@ TcTuning g_tune = [] {
 }();
 }  // namespace
 
-int accum_chunks(int64_t lpad, int nkb) {
+int accum_chunks(int64_t lpad) {
   const TcTuning t = tc_tuning();
-  if (lpad <= t.one_acc_l || nkb < 2) return 1;
+  const int64_t groups = lpad / 64;  // chunks are whole 64-sample groups
+  if (lpad <= t.one_acc_l || groups < 2) return 1;
   int64_t c = (lpad + t.chunk_l - 1) / t.chunk_l;
   if (c < 2) c = 2;
-  if (c > nkb) c = nkb;
+  if (c > groups) c = groups;
   return (int)c;
 }
 
@@ -612,15 +615,28 @@ pcc_status pcc_perm_test(const pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                    static_cast<cudaStream_t>(stream));
 }
 
-pcc_status pcc_allpairs_upper_batched(const pcc_zmat* const* Zs, int32_t B,
-                                      float* const* Rs, void* stream) {
+pcc_status pcc_allpairs_upper_batched_tuned(const pcc_zmat* const* Zs,
+                                            int32_t B, float* const* Rs,
+                                            const int32_t* pair,
+                                            const int32_t* band_rows,
+                                            void* stream) {
   if (!Zs || !Rs || B < 1 || B > (1 << 20)) return PCC_ERR_INVALID_ARG;
   for (int32_t b = 0; b < B; ++b) {
     if (!Zs[b] || !Rs[b] || !is_split(Zs[b]->prec) ||
         Zs[b]->device != Zs[0]->device)
       return PCC_ERR_INVALID_ARG;
+    if (pair && pair[b] != 0 && pair[b] != 1) return PCC_ERR_INVALID_ARG;
+    if (band_rows && (band_rows[b] < 1 || band_rows[b] > 4096))
+      return PCC_ERR_INVALID_ARG;
   }
-  return allpairs_batched(Zs, B, Rs, static_cast<cudaStream_t>(stream));
+  return allpairs_batched(Zs, B, Rs, pair, band_rows,
+                          static_cast<cudaStream_t>(stream));
+}
+
+pcc_status pcc_allpairs_upper_batched(const pcc_zmat* const* Zs, int32_t B,
+                                      float* const* Rs, void* stream) {
+  return pcc_allpairs_upper_batched_tuned(Zs, B, Rs, nullptr, nullptr,
+                                          stream);
 }
 
 pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,

@@ -87,10 +87,10 @@ struct TcTuning {
 };
 TcTuning tc_tuning();
 void tc_set_tuning(const TcTuning& t);
-// Accumulator chunks of a work unit with padded rows of lpad samples in nkb
-// K blocks (tc_common.cuh): 1 up to one_acc_l samples, else enough chunks of
-// at most chunk_l samples (at least 2, at most nkb).
-int accum_chunks(int64_t lpad, int nkb);
+// Accumulator chunks of a work unit with padded rows of lpad samples
+// (tc_common.cuh): 1 up to one_acc_l samples, else enough chunks of at most
+// chunk_l samples (at least 2, at most lpad / 64), whatever the stage size.
+int accum_chunks(int64_t lpad);
 
 // K1: standardize rows of X into Z's storage.
 cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
@@ -151,9 +151,12 @@ pcc_status allpairs_host(const pcc_zmat* ZA, const pcc_zmat* ZB, void* host,
                          pcc_rows_sink sink, void* user, cudaStream_t s,
                          const HostEdges* he = nullptr);
 
-// K7: all pairs of B matrices in one persistent launch.
+// K7: all pairs of B matrices in one persistent launch per CTA form; pair
+// and band (B entries each, or NULL for the current tuning) choose each
+// matrix's form (1 = 2-SM CTA pairs) and band rows.
 pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
-                            float* const* Rs, cudaStream_t s);
+                            float* const* Rs, const int32_t* pair,
+                            const int32_t* band, cudaStream_t s);
 
 // K6: permutation test over permutations [k0, k1) of d_perms (P x l).
 pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,

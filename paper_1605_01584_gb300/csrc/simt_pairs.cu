@@ -117,36 +117,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
   }
 
   V ra[NV], rb[NV];
+  // thread -> (row, group of VW k values): four neighbouring threads read
+  // 64 contiguous bytes of one row (coalesced); the transposed stores
+  // As[k][r] of a warp then cover 8 rows at 4 k groups, and for FP32 the
+  // k rows 8..15 keep their columns XOR 8 (whole float4 groups move) so
+  // that those 4 groups fall on distinct banks (row pitch BT + 4 words)
+  auto swz = [](int k) { return sizeof(T) == 4 ? ((k >> 3) & 1) * 8 : 0; };
+  // a thread's NV vectors are rows r0, r0 + RV, ... at one k group
+  constexpr int RV = 256 / (BK / VW);  // rows covered by one vector round
+  const int r0 = tid / (BK / VW);
+  const int kq0 = (tid % (BK / VW)) * VW;
+  const T* __restrict__ pa = Z + (row0 + r0) * lpad + kq0;
+  const T* __restrict__ pb = Zb + (col0 + r0) * lpad + kq0;
+  const int64_t vstride = (int64_t)RV * lpad;
   auto gload = [&](int64_t kb) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const int idx = tid + 256 * v;
-      const int r = idx / (BK / VW);
-      const int kq = (idx % (BK / VW)) * VW;
-      const int64_t k = kb * BK + kq;
-      V za, zb;
-      if (row0 + r < n)
-        za = *reinterpret_cast<const V*>(Z + (row0 + r) * lpad + k);
-      else
-        za = V{};
-      if (col0 + r < nb)
-        zb = *reinterpret_cast<const V*>(Zb + (col0 + r) * lpad + k);
-      else
-        zb = V{};
-      ra[v] = za;
-      rb[v] = zb;
+      const int64_t off = v * vstride + kb * BK;
+      ra[v] = (row0 + r0 + v * RV < n)
+                  ? *reinterpret_cast<const V*>(pa + off) : V{};
+      rb[v] = (col0 + r0 + v * RV < nb)
+                  ? *reinterpret_cast<const V*>(pb + off) : V{};
     }
   };
   auto sstore = [&](int buf) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const int idx = tid + 256 * v;
-      const int r = idx / (BK / VW);
-      const int kq = (idx % (BK / VW)) * VW;
+      const int r = r0 + v * RV;
+      const int kq = kq0;
 #pragma unroll
       for (int q = 0; q < VW; ++q) {
-        As[buf][kq + q][r] = vget<V, T>(ra[v], q);
-        Bs[buf][kq + q][r] = vget<V, T>(rb[v], q);
+        As[buf][kq + q][r ^ swz(kq + q)] = vget<V, T>(ra[v], q);
+        Bs[buf][kq + q][r ^ swz(kq + q)] = vget<V, T>(rb[v], q);
       }
     }
   };
@@ -167,10 +169,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T a[TT], b[TT];
-      const VH a0 = *reinterpret_cast<const VH*>(&As[cur][k][ty * H]);
-      const VH a1 = *reinterpret_cast<const VH*>(&As[cur][k][BT / 2 + ty * H]);
-      const VH b0 = *reinterpret_cast<const VH*>(&Bs[cur][k][tx * H]);
-      const VH b1 = *reinterpret_cast<const VH*>(&Bs[cur][k][BT / 2 + tx * H]);
+      const int sw = swz(k);
+      const VH a0 =
+          *reinterpret_cast<const VH*>(&As[cur][k][(ty * H) ^ sw]);
+      const VH a1 =
+          *reinterpret_cast<const VH*>(&As[cur][k][(BT / 2 + ty * H) ^ sw]);
+      const VH b0 =
+          *reinterpret_cast<const VH*>(&Bs[cur][k][(tx * H) ^ sw]);
+      const VH b1 =
+          *reinterpret_cast<const VH*>(&Bs[cur][k][(BT / 2 + tx * H) ^ sw]);
 #pragma unroll
       for (int q = 0; q < H; ++q) {
         a[q] = vget<VH, T>(a0, q);

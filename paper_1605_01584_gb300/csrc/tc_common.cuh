@@ -6,8 +6,9 @@
 // accumulator with a rounding toward zero, so the error of a running sum
 // grows with the number of updates made while it is large (on rows whose
 // mass sits in one sample, r = 1, about 9e-9 per sample of the row after
-// that sample).  A unit's K blocks are therefore cut into nch chunks; chunk
-// c accumulates blocks [c*nkb/nch, (c+1)*nkb/nch) into a fresh TMEM buffer,
+// that sample).  A unit's K blocks are therefore cut into nch chunks of
+// nearly equal length (whole groups of 64 samples), each accumulated into a
+// fresh TMEM buffer,
 // the two buffers alternating from chunk to chunk, and the epilogue adds
 // each finished chunk into the next one with one round-to-nearest FP32 add
 // per element (fold_acc) before that buffer is handed back.  nch = 1 keeps
@@ -20,9 +21,16 @@
 
 namespace pcc {
 
-// first K block of chunk c of a unit of nkb blocks cut into nch chunks
+// First K block of chunk c of a unit of nkb blocks of KB samples cut into
+// nch chunks.  Boundaries are set in groups of 64 samples (padded rows are
+// a multiple of 64), so every stage size (KB = 32 or 64) cuts a row at the
+// same samples and gives the same bits.
+template <int KB>
 __host__ __device__ __forceinline__ int chunk_begin(int nkb, int nch, int c) {
-  return (int)((int64_t)c * nkb / nch);
+  static_assert(KB == 32 || KB == 64, "stage sizes");
+  constexpr int per64 = 64 / KB;
+  const int64_t groups = nkb / per64;
+  return (int)((int64_t)c * groups / nch) * per64;
 }
 
 // Every fill of the ring, per stage: how many fills the producer issued and

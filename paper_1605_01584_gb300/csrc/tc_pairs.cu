@@ -52,8 +52,8 @@
 // a third smaller (six stages instead of four).  Both CTAs' copies count on
 // the even CTA's stage barrier; its commits release the stage in both CTAs
 // and hand each CTA its half of the accumulator; both epilogues release the
-// accumulator to the even CTA.  Otherwise (pcc_set_pair_mma(0), or K = 64
-// stages) every CTA runs its own M = 128 MMA over all 256 B rows.
+// accumulator to the even CTA.  Otherwise (pcc_set_pair_mma(0)) every CTA
+// runs its own M = 128 MMA over all 256 B rows.
 // Measured at 65,536 x 512: 4.76 ms (2-SM MMA), 5.42 ms (independent CTAs).
 // Every wait is bounded (pcc_ptx.cuh): a wait that runs out records
 // PCC_ERR_TIMEOUT; the CTA stops issuing, waits for every copy it (and, in
@@ -110,7 +110,8 @@ struct TcParams {
 // stages of 96 KB) or 32 (64-B swizzle, 4 stages of 48 KB: the same bytes in
 // flight, refilled at half the granularity).
 // PAIR (the 2-SM MMA of a CTA pair): each CTA holds only its 128 of the
-// 256 B rows, so a stage is a third smaller and the ring holds six.
+// 256 B rows, so a stage is a third smaller and the ring holds six (K = 32)
+// or three (K = 64).
 template <int NPROD, int KB, bool PAIR = false>
 struct Cfg {
   static constexpr int kTileA = kBM * KB * 2;
@@ -156,7 +157,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   // B operand maps: the second matrix's for CROSS, else Z's own
   const CUtensorMap* mb_hi = CROSS ? &tmb_hi : &tm_hi;
   const CUtensorMap* mb_lo = CROSS ? &tmb_lo : &tm_lo;
-  static_assert(!PAIR || KB == 32, "the 2-SM MMA form uses K = 32 stages");
   using C = Cfg<NPROD, KB, PAIR>;
   constexpr int kTileA = C::kTileA;
   constexpr int kTileB = C::kTileB;
@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kBN);
-          const int kb0 = chunk_begin(nkb, nch, c);
-          const int kb1 = chunk_begin(nkb, nch, c + 1);
+          const int kb0 = chunk_begin<KB>(nkb, nch, c);
+          const int kb1 = chunk_begin<KB>(nkb, nch, c + 1);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&full[stage], phase, w)) {
               ok = false;
@@ -491,10 +491,10 @@ cudaError_t launch_inst(const pcc_zmat* Z, const pcc_zmat* ZB,
   const CUtensorMap& tbl = KB == 64 ? ZB->tm_lo : ZB->tm_lo32;
   const int64_t tiles = (p.u_end - p.u_begin) / 2;
   const TcTuning tn = tc_tuning();
-  if constexpr (KB == 32) {
+  {
     if (tn.cluster == 2 && tn.pair_mma != 0 && tiles >= 2) {
-      auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, 32, CROSS, true>;
-      const int smem = Cfg<NPROD, 32, true>::kSmemBytes;
+      auto fn = k_pairs_tc<NPROD, BF16, WRITE_R, EDGES, KB, CROSS, true>;
+      const int smem = Cfg<NPROD, KB, true>::kSmemBytes;
       cudaError_t e =
           ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
       if (e != cudaSuccess) return e;
@@ -553,7 +553,7 @@ template <int KB, bool CROSS>
 cudaError_t launch_kb(const pcc_zmat* Z, const pcc_zmat* ZB, TcParams& p,
                       int grid, bool write_r, bool edges_on, cudaStream_t s) {
   p.nkb = (int)(Z->lpad / KB);
-  p.nch = accum_chunks(Z->lpad, p.nkb);
+  p.nch = accum_chunks(Z->lpad);
   switch (Z->prec) {
     case PCC_PREC_BF16X3:
       return launch_prec<3, true, KB, CROSS>(Z, ZB, p, grid, write_r,
@@ -646,6 +646,8 @@ cudaError_t launch_tc_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, float* R,
   const int64_t units = p.u_end - p.u_begin;
   int grid = num_sms(ZA->device);
   if (units < grid) grid = (int)units;
+  if (tc_tuning().stage_k == 64)
+    return launch_kb<64, true>(ZA, ZB, p, grid, R != nullptr, edges_on, s);
   return launch_kb<32, true>(ZA, ZB, p, grid, R != nullptr, edges_on, s);
 }
 

@@ -33,9 +33,8 @@ def test_tune_small_shape_and_apply(pcc_gpu, tmp_path):
     before = pcc.pcc_get_tuning()
     e = autotune.tune_pairs(2048, 128, "bf16x3", reps=2, path=p,
                             candidates={"band_rows": (8, 32)})
-    # (K = 32, CTA pairs), (K = 32, single CTAs), (K = 64, single CTAs)
-    # at each of the two band heights
-    assert len(e["all"]) == 6 and e["best"]["ms"] > 0
+    # K = 32 or 64 stages x CTA pairs or single CTAs x two band heights
+    assert len(e["all"]) == 8 and e["best"]["ms"] > 0
     assert pcc.pcc_get_tuning() == before  # tuning run restores the knobs
     X = torch.rand((2048, 128), device="cuda")
     Z = pcc.pcc_standardize(X, "bf16x3")
@@ -66,3 +65,19 @@ def test_lookup_skips_unusable_entries():
     assert autotune.lookup(65536, 512, "bf16x3", cache) == good["best"]
     assert autotune.lookup(65536, 512, "fp16x3s", cache) is None
     assert autotune.lookup(65536, 512, "bf16x3", {}) is None
+
+
+def test_lookup_batched_takes_the_best_k32_run():
+    runs = [{"stage_k": 64, "cluster": 1, "pair_mma": 0, "band_rows": 8,
+             "ms": 1.0},
+            {"stage_k": 32, "cluster": 1, "pair_mma": 0, "band_rows": 16,
+             "ms": 1.2},
+            {"stage_k": 32, "cluster": 2, "pair_mma": 1, "band_rows": 32,
+             "ms": 1.1}]
+    cache = {"n4096_l512_fp16x3s": {"best": runs[0], "all": runs}}
+    assert autotune.lookup_batched(4096, 500, "fp16x3s", cache) == (1, 32)
+    # nearest n in the same (padded l, form) bucket
+    assert autotune.lookup_batched(3000, 512, "fp16x3s", cache) == (1, 32)
+    assert autotune.lookup_batched(4096, 700, "fp16x3s", cache) is None
+    cache["n4096_l512_fp16x3s"]["all"] = runs[:1]  # no K = 32 run
+    assert autotune.lookup_batched(4096, 512, "fp16x3s", cache) is None

@@ -260,3 +260,102 @@ def test_standardize_batched_invalid_arguments(pcc_gpu):
         pcc.pcc_standardize_batched([good, bad])
     with pytest.raises(pcc.PccError):
         pcc.pcc_standardize_batched([])
+
+
+TUNED = [(1100, 300, "fp16x3s"), (700, 1100, "fp16x3s"), (2049, 96, "bf16x3"),
+         (520, 64, "fp16x3s")]
+CHOICES = [(1, 2), (0, 5), (0, 1), (1, 32)]  # (pair, band rows) per matrix
+
+
+def _single(pcc, Z, R, pair, band):
+    """pcc_allpairs_upper of one matrix under the given form and band."""
+    torch = _torch()
+    old = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(stage_k=32, cluster=2 if pair else 1,
+                           band_rows=band, pair_mma=pair)
+        out = torch.full_like(R, 7.0)
+        pcc.pcc_allpairs_upper(Z, out)
+        assert pcc.pcc_sync_status(Z) == 0
+    finally:
+        pcc.pcc_set_tuning(old["stage_k"], old["cluster"], old["band_rows"],
+                           pair_mma=old["pair_mma"])
+    return out.cpu().numpy()
+
+
+def test_batched_per_matrix_choices(pcc_gpu):
+    """Matrices of one batch under different tuned shapes (CTA pairs or
+    single CTAs, band rows 1 to 32): two persistent launches, each matrix
+    bit-equal to its single run under the same choice and within 1e-5 of
+    the oracle; graph replay of the tuned call gives the same bits."""
+    torch = _torch()
+    pcc = pcc_gpu
+    Xs, Zs, Rs = _setup(pcc, TUNED, seed0=950)
+    used = pcc.pcc_allpairs_upper_batched(Zs, Rs, choices=CHOICES)
+    assert used == CHOICES
+    assert pcc.pcc_sync_status(Zs[0]) == 0
+    first = [R.cpu().numpy() for R in Rs]
+    for b, (n, l, prec) in enumerate(TUNED):
+        got = first[b]
+        assert not np.any(got == 7.0), b
+        single = _single(pcc, Zs[b], Rs[b], *CHOICES[b])
+        assert np.array_equal(np.isnan(got), np.isnan(single))
+        ok = ~np.isnan(got)
+        assert np.array_equal(got[ok].view(np.uint32),
+                              single[ok].view(np.uint32)), b
+        want = oracle.pcc_upper(Xs[b])
+        assert np.array_equal(np.isnan(got), np.isnan(want))
+        assert np.max(np.abs(got[ok] - want[ok])) <= 1e-5, b
+    for R in Rs:
+        R.fill_(7.0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pcc.pcc_allpairs_upper_batched(Zs, Rs, choices=CHOICES)
+    g.replay()
+    torch.cuda.synchronize()
+    for b in range(len(TUNED)):
+        got = Rs[b].cpu().numpy()
+        ok = ~np.isnan(got)
+        assert np.array_equal(got[ok].view(np.uint32),
+                              first[b][ok].view(np.uint32)), b
+
+
+def test_batched_default_consults_the_tune_cache(pcc_gpu):
+    """With a tune cache holding entries for some shapes, the default call
+    gives those matrices the cached best (K = 32) choice and the rest the
+    current knobs."""
+    pcc = pcc_gpu
+    from paper_1605_01584_gb300 import autotune
+    Xs, Zs, Rs = _setup(pcc, TUNED, seed0=960)
+    cache = {}
+    for (n, l, prec), (pair, band) in zip(TUNED[:2], [(0, 4), (1, 16)]):
+        cache[autotune.bucket(n, l, prec)] = {
+            "best": {"stage_k": 64, "cluster": 1, "band_rows": 8,
+                     "pair_mma": 0, "ms": 0.5},
+            "all": [{"stage_k": 64, "cluster": 1, "pair_mma": 0,
+                     "band_rows": 8, "ms": 0.5},
+                    {"stage_k": 32, "cluster": 2 if pair else 1,
+                     "pair_mma": pair, "band_rows": band, "ms": 0.6},
+                    {"stage_k": 32, "cluster": 1, "pair_mma": 0,
+                     "band_rows": 64, "ms": 0.9}]}
+    t = pcc.pcc_get_tuning()
+    default = (1 if t["pair_mma"] and t["cluster"] == 2 else 0,
+               t["band_rows"])
+    used = pcc.pcc_allpairs_upper_batched(Zs, Rs, cache=cache)
+    assert used == [(0, 4), (1, 16), default, default]
+    assert pcc.pcc_sync_status(Zs[0]) == 0
+    for b in range(len(TUNED)):
+        got = Rs[b].cpu().numpy()
+        single = _single(pcc, Zs[b], Rs[b], *used[b])
+        ok = ~np.isnan(got)
+        assert np.array_equal(got[ok].view(np.uint32),
+                              single[ok].view(np.uint32)), b
+
+
+def test_batched_rejects_bad_choices(pcc_gpu):
+    pcc = pcc_gpu
+    _, Zs, Rs = _setup(pcc, TUNED[:2], seed0=970)
+    for bad in ([(2, 8), (1, 8)], [(1, 0), (1, 8)], [(1, 5000), (0, 8)]):
+        with pytest.raises(pcc.PccError) as e:
+            pcc.pcc_allpairs_upper_batched(Zs, Rs, choices=bad)
+        assert e.value.status == pcc.PCC_ERR_INVALID_ARG

@@ -166,3 +166,26 @@ def test_pair_mma_cross(pcc_gpu):
         got = run()
     assert not np.any(got == SENT)
     _same_bits(got, ref, "cross")
+
+
+@pytest.mark.parametrize("n,l", [(1000, 130), (700, 1500)])
+def test_pair_mma_k64_stages_equal_k32_bits(pcc_gpu, n, l):
+    """The pair form with K = 64 stages (three 64 KB stages, 128-byte
+    swizzle) issues the same MMAs in the same K order as K = 32 stages, and
+    accumulator chunks end at the same samples for both (l = 1,500: three
+    chunks), so the results are the same bits."""
+    import torch
+    pcc = pcc_gpu
+    X = torch.from_numpy(_data(n, l, 86 + l)).cuda()
+    Z = pcc.pcc_standardize(X, "fp16x3s")
+    old = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(stage_k=32, cluster=1, pair_mma=0)
+        ref = _upper(pcc, Z, n)
+        pcc.pcc_set_tuning(stage_k=64, cluster=2, pair_mma=1)
+        got = _upper(pcc, Z, n)
+    finally:
+        pcc.pcc_set_tuning(old["stage_k"], old["cluster"], old["band_rows"],
+                           pair_mma=old["pair_mma"])
+    assert not np.any(got == SENT)
+    _same_bits(got, ref, f"K=64 pair {n}x{l}")
