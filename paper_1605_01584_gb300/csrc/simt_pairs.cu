@@ -8,8 +8,8 @@
 // tile, r(i,j) = sum_k z_i[k] z_j[k] (Eq. (6)) for rows y in
 // [yt*BT, (yt+1)*BT) and columns x in [xt*BT, (xt+1)*BT); pairs with
 // x <= y are skipped (Algorithm 1 skips y > x; the diagonal is excluded
-// here).  Instead of one thread per column (the Xeon Phi layout), 256
-// threads each own a TT x TT register block, K is staged through shared
+// here).  Instead of one thread per column (the Xeon Phi layout), the
+// threads each own a register block of the tile, K is staged through shared
 // memory BK at a time with a register prefetch of the next stage.
 //
 // CROSS: the non-symmetric job matrix between the rows of two matrices A
@@ -37,17 +37,6 @@ struct Vec16<double> {
   static constexpr int W = 2;
 };
 
-template <typename T, int H>
-struct VecH;
-template <>
-struct VecH<float, 4> {
-  using type = float4;
-};
-template <>
-struct VecH<double, 2> {
-  using type = double2;
-};
-
 template <typename V, typename T>
 __device__ __forceinline__ T vget(const V& v, int q);
 template <>
@@ -69,11 +58,17 @@ struct SimtCross {
   int64_t r_off;           // R holds the output from element r_off on
 };
 
-template <typename T, typename OutT, int BT, int TT, int BK, bool WRITE_R,
-          bool EDGES, bool CROSS>
-// FP32: two blocks per SM (at one, with 129 registers, the eight warps of a
-// block idle together at every stage barrier); FP64: three
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
+// Thread layout: NT threads as 16 columns (tx) x NT/16 rows (ty) of
+// threads; with W = 16 bytes / sizeof(T) (one vector), thread (tx, ty) owns
+// the W x W blocks at rows g * BT/GR + ty * W (g < GR groups) and columns
+// h * BT/2 + tx * W (h < 2): TR = GR * W rows by TC = 2 * W columns, read per
+// k as GR + 2 vectors of shared memory.  FP32 runs 256 threads of 8 x 8,
+// FP64 256 threads of 4 x 4.  (128 FP32 threads of 16 x 8, 6 vector loads
+// per 128 FMAs instead of 4 per 64, took 50.8 ms at 65,536 x 512 against
+// 46.6: two blocks of 4 warps per SM hide less than two of 8.)
+template <typename T, typename OutT, int BT, int GR, int NT, int BK,
+          bool WRITE_R, bool EDGES, bool CROSS>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 3)
     k_pairs_simt(const T* __restrict__ Z, const uint8_t* __restrict__ flags,
                  int64_t n, int64_t lpad, int64_t m, int64_t t0,
                  OutT* __restrict__ R, float tau, pcc_edge* __restrict__ edges,
@@ -82,13 +77,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
   const T* __restrict__ Zb = CROSS ? static_cast<const T*>(cx.Zb) : Z;
   const uint8_t* __restrict__ flagsb = CROSS ? cx.flagsb : flags;
   const int64_t nb = CROSS ? cx.nb : n;
-  static_assert((BT / TT) * (BT / TT) == 256, "256 threads per tile");
-  constexpr int H = TT / 2;
-  constexpr int PAD = 4;
   using V = typename Vec16<T>::type;
-  constexpr int VW = Vec16<T>::W;
-  constexpr int NV = BT * BK / 256 / VW;  // vector loads per thread/operand
-  using VH = typename VecH<T, H>::type;
+  constexpr int W = Vec16<T>::W;        // elements per 16-byte vector
+  constexpr int NTY = NT / 16;          // thread rows
+  constexpr int TR = GR * W, TC = 2 * W;
+  static_assert(NTY * W * GR == BT && 16 * W * 2 == BT, "thread layout");
+  constexpr int PAD = 4;
+  constexpr int NV = BT * BK / NT / W;  // vector loads per thread/operand
+  constexpr int NWARP = NT / 32;
 
   // operand stages; after the K loop the same memory stages the tile for
   // the stores, half of its rows at a time
@@ -111,22 +107,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
   }
   const int64_t row0 = yt * BT, col0 = xt * BT;
 
-  if (tid < BT) {
-    fr[tid] = (row0 + tid < n) ? flags[row0 + tid] : 1;
-    fc[tid] = (col0 + tid < nb) ? flagsb[col0 + tid] : 1;
+  for (int t = tid; t < BT; t += NT) {
+    fr[t] = (row0 + t < n) ? flags[row0 + t] : 1;
+    fc[t] = (col0 + t < nb) ? flagsb[col0 + t] : 1;
   }
 
   V ra[NV], rb[NV];
-  // thread -> (row, group of VW k values): four neighbouring threads read
+  // thread -> (row, group of W k values): four neighbouring threads read
   // 64 contiguous bytes of one row (coalesced); the transposed stores
   // As[k][r] of a warp then cover 8 rows at 4 k groups, and for FP32 the
   // k rows 8..15 keep their columns XOR 8 (whole float4 groups move) so
   // that those 4 groups fall on distinct banks (row pitch BT + 4 words)
   auto swz = [](int k) { return sizeof(T) == 4 ? ((k >> 3) & 1) * 8 : 0; };
   // a thread's NV vectors are rows r0, r0 + RV, ... at one k group
-  constexpr int RV = 256 / (BK / VW);  // rows covered by one vector round
-  const int r0 = tid / (BK / VW);
-  const int kq0 = (tid % (BK / VW)) * VW;
+  constexpr int RV = NT / (BK / W);  // rows covered by one vector round
+  const int r0 = tid / (BK / W);
+  const int kq0 = (tid % (BK / W)) * W;
   const T* __restrict__ pa = Z + (row0 + r0) * lpad + kq0;
   const T* __restrict__ pb = Zb + (col0 + r0) * lpad + kq0;
   const int64_t vstride = (int64_t)RV * lpad;
@@ -144,20 +140,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int r = r0 + v * RV;
-      const int kq = kq0;
 #pragma unroll
-      for (int q = 0; q < VW; ++q) {
-        As[buf][kq + q][r ^ swz(kq + q)] = vget<V, T>(ra[v], q);
-        Bs[buf][kq + q][r ^ swz(kq + q)] = vget<V, T>(rb[v], q);
+      for (int q = 0; q < W; ++q) {
+        As[buf][kq0 + q][r ^ swz(kq0 + q)] = vget<V, T>(ra[v], q);
+        Bs[buf][kq0 + q][r ^ swz(kq0 + q)] = vget<V, T>(rb[v], q);
       }
     }
   };
 
-  T acc[TT][TT];
+  T acc[TR][TC];
 #pragma unroll
-  for (int a = 0; a < TT; ++a)
+  for (int a = 0; a < TR; ++a)
 #pragma unroll
-    for (int b = 0; b < TT; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < TC; ++b) acc[a][b] = T(0);
 
   const int64_t nkb = lpad / BK;
   gload(0);
@@ -168,27 +163,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
     if (kb + 1 < nkb) gload(kb + 1);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      T a[TT], b[TT];
+      T a[TR], b[TC];
       const int sw = swz(k);
-      const VH a0 =
-          *reinterpret_cast<const VH*>(&As[cur][k][(ty * H) ^ sw]);
-      const VH a1 =
-          *reinterpret_cast<const VH*>(&As[cur][k][(BT / 2 + ty * H) ^ sw]);
-      const VH b0 =
-          *reinterpret_cast<const VH*>(&Bs[cur][k][(tx * H) ^ sw]);
-      const VH b1 =
-          *reinterpret_cast<const VH*>(&Bs[cur][k][(BT / 2 + tx * H) ^ sw]);
 #pragma unroll
-      for (int q = 0; q < H; ++q) {
-        a[q] = vget<VH, T>(a0, q);
-        a[H + q] = vget<VH, T>(a1, q);
-        b[q] = vget<VH, T>(b0, q);
-        b[H + q] = vget<VH, T>(b1, q);
+      for (int g = 0; g < GR; ++g) {
+        const V v = *reinterpret_cast<const V*>(
+            &As[cur][k][(g * (BT / GR) + ty * W) ^ sw]);
+#pragma unroll
+        for (int q = 0; q < W; ++q) a[g * W + q] = vget<V, T>(v, q);
       }
 #pragma unroll
-      for (int i = 0; i < TT; ++i)
+      for (int h = 0; h < 2; ++h) {
+        const V v = *reinterpret_cast<const V*>(
+            &Bs[cur][k][(h * (BT / 2) + tx * W) ^ sw]);
 #pragma unroll
-        for (int j = 0; j < TT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int q = 0; q < W; ++q) b[h * W + q] = vget<V, T>(v, q);
+      }
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TC; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     if (kb + 1 < nkb) {
       sstore(cur ^ 1);
@@ -198,30 +192,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
 
   // Stores: each half of the tile's rows goes through shared memory, so
   // that a warp writes 32 consecutive pairs of one row per instruction (a
-  // packed row's pairs are contiguous; thread blocks of 8 x 8 in registers
-  // would touch 16 sectors per store instruction).
+  // packed row's pairs are contiguous; the threads' register blocks would
+  // touch 16 sectors per store instruction).
   const int lane = tid & 31, warp = tid >> 5;
   T(*tile)[BT + PAD] = reinterpret_cast<T(*)[BT + PAD]>(smem_ops);
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     __syncthreads();  // operand stages (or the previous half) are free
+    // row groups g of this half: g * BT/GR in [half * BT/2, (half+1) BT/2)
 #pragma unroll
-    for (int a = 0; a < H; ++a) {
-      const int li = ty * H + a;  // row within the half
-      const T* q = acc[half * H + a];
-      VH v0, v1;
-      if constexpr (H == 4) {
-        v0 = make_float4(q[0], q[1], q[2], q[3]);
-        v1 = make_float4(q[4], q[5], q[6], q[7]);
-      } else {
-        v0 = make_double2(q[0], q[1]);
-        v1 = make_double2(q[2], q[3]);
+    for (int g = half * GR / 2; g < (half + 1) * GR / 2; ++g) {
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const int li = g * (BT / GR) - half * (BT / 2) + ty * W + a;
+        const T* q = acc[g * W + a];
+        V v0, v1;
+        if constexpr (W == 4) {
+          v0 = make_float4(q[0], q[1], q[2], q[3]);
+          v1 = make_float4(q[4], q[5], q[6], q[7]);
+        } else {
+          v0 = make_double2(q[0], q[1]);
+          v1 = make_double2(q[2], q[3]);
+        }
+        *reinterpret_cast<V*>(&tile[li][tx * W]) = v0;
+        *reinterpret_cast<V*>(&tile[li][BT / 2 + tx * W]) = v1;
       }
-      *reinterpret_cast<VH*>(&tile[li][tx * H]) = v0;
-      *reinterpret_cast<VH*>(&tile[li][BT / 2 + tx * H]) = v1;
     }
     __syncthreads();
-    for (int li = warp; li < BT / 2; li += 8) {
+    for (int li = warp; li < BT / 2; li += NWARP) {
       const int ri = half * (BT / 2) + li;  // row within the tile
       const int64_t i = row0 + ri;
       if (i >= n) break;
@@ -266,7 +264,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 3)
   }
 }
 
-template <typename T, typename OutT, int BT, int TT, bool CROSS>
+template <typename T, typename OutT, int BT, int GR, int NT, bool CROSS>
 cudaError_t launch_t(const pcc_zmat* Z, OutT* R, int64_t t0, int64_t t1,
                      bool edges_on, float tau, pcc_edge* edges, uint64_t cap,
                      unsigned long long* count, cudaStream_t s,
@@ -277,18 +275,18 @@ cudaError_t launch_t(const pcc_zmat* Z, OutT* R, int64_t t0, int64_t t1,
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const T* z = reinterpret_cast<const T*>(Z->z);
   if (edges_on && R)
-    k_pairs_simt<T, OutT, BT, TT, 16, true, true, CROSS>
-        <<<(unsigned)nblocks, 256, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
+    k_pairs_simt<T, OutT, BT, GR, NT, 16, true, true, CROSS>
+        <<<(unsigned)nblocks, NT, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
                                            R, tau, edges, cap, count,
                                            Z->status, cx);
   else if (edges_on)
-    k_pairs_simt<T, OutT, BT, TT, 16, false, true, CROSS>
-        <<<(unsigned)nblocks, 256, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
+    k_pairs_simt<T, OutT, BT, GR, NT, 16, false, true, CROSS>
+        <<<(unsigned)nblocks, NT, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
                                            R, tau, edges, cap, count,
                                            Z->status, cx);
   else
-    k_pairs_simt<T, OutT, BT, TT, 16, true, false, CROSS>
-        <<<(unsigned)nblocks, 256, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
+    k_pairs_simt<T, OutT, BT, GR, NT, 16, true, false, CROSS>
+        <<<(unsigned)nblocks, NT, 0, s>>>(z, Z->flags, Z->n, Z->lpad, m, t0,
                                            R, tau, edges, cap, count,
                                            Z->status, cx);
   return cudaGetLastError();
@@ -301,14 +299,14 @@ cudaError_t launch_prec(const pcc_zmat* Z, void* R, pcc_dtype rt, int64_t t0,
                         const SimtCross& cx) {
   const bool edges_on = count != nullptr;
   if (Z->prec == PCC_PREC_FP32)
-    return launch_t<float, float, 128, 8, CROSS>(
+    return launch_t<float, float, 128, 2, 256, CROSS>(
         Z, reinterpret_cast<float*>(R), t0, t1, edges_on, tau, edges, cap,
         count, s, cx);
   if (rt == PCC_F64)
-    return launch_t<double, double, 64, 4, CROSS>(
+    return launch_t<double, double, 64, 2, 256, CROSS>(
         Z, reinterpret_cast<double*>(R), t0, t1, edges_on, tau, edges, cap,
         count, s, cx);
-  return launch_t<double, float, 64, 4, CROSS>(Z, reinterpret_cast<float*>(R),
+  return launch_t<double, float, 64, 2, 256, CROSS>(Z, reinterpret_cast<float*>(R),
                                                t0, t1, edges_on, tau, edges,
                                                cap, count, s, cx);
 }
