@@ -379,8 +379,8 @@ pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
  *   stage_k    K per shared-memory ring stage: 32 (4 stages; 6 in the 2-SM
  *              pair form, whose stages are a third smaller) or 64 (2; 3 in
  *              the pair form; the default, PCC_TC_BK=32 in the environment
- *              selects 32 when the library loads).  The batched and
- *              permutation kernels always use K = 32.
+ *              selects 32 when the library loads).  The batched kernel
+ *              follows it too; the permutation kernel always uses K = 32.
  *   cluster    2 = CTA pairs running one 2-SM MMA (while
  *              pcc_set_pair_mma is on), 1 = independent CTAs.
  *   band_rows  super-tile rows per band of the pair schedule (rows of a

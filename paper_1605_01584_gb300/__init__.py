@@ -472,7 +472,7 @@ def pcc_allpairs_upper_batched(Zs, Rs, stream=None, choices="auto",
             info = z.info()
             form = _FORM_NAMES.get(info["prec"])  # others: rejected below
             b = None if form is None else autotune.lookup_batched(
-                info["n"], info["l"], form, c)
+                info["n"], info["l"], form, c, stage_k=t["stage_k"])
             used.append(b if b is not None else default)
     else:
         used = [(int(p), int(g)) for p, g in choices]

@@ -99,10 +99,11 @@ def lookup(n: int, l: int, prec: str, cache: dict | None = None):
     return best
 
 
-def lookup_batched(n: int, l: int, prec: str, cache: dict | None = None):
+def lookup_batched(n: int, l: int, prec: str, cache: dict | None = None,
+                   stage_k: int = 64):
     """(pair, band_rows) for one matrix of a batched launch: the fastest
-    timed candidate with K = 32 stages (the batched kernel's) in the entry
-    lookup() would use; None without one."""
+    timed candidate with the batched kernel's stage size (stage_k, the
+    current knob) in the entry lookup() would use; None without one."""
     cache = load_cache() if cache is None else cache
     key = bucket(n, l, prec)
     entry = cache.get(key) if _usable(cache.get(key)) else None
@@ -119,7 +120,8 @@ def lookup_batched(n: int, l: int, prec: str, cache: dict | None = None):
     if entry is None:
         return None
     runs = [r for r in entry.get("all", []) if isinstance(r, dict) and
-            r.get("stage_k") == 32 and isinstance(r.get("ms"), (int, float))]
+            r.get("stage_k") == stage_k and
+            isinstance(r.get("ms"), (int, float))]
     if not runs:
         return None
     b = min(runs, key=lambda r: r["ms"])
@@ -128,17 +130,18 @@ def lookup_batched(n: int, l: int, prec: str, cache: dict | None = None):
 
 def tune_batched(shapes, prec: str = "auto", reps: int = 3,
                  bands=(8, 16, 32), path: str | None = None) -> dict:
-    """Tune every distinct shape bucket of a batch (K = 32 stages, CTA pairs
-    or single CTAs, the given band heights) on a synthetic matrix of the
-    first shape of that bucket, and cache the results; returns bucket ->
-    entry."""
+    """Tune every distinct shape bucket of a batch (the current stage size,
+    CTA pairs or single CTAs, the given band heights) on a synthetic matrix
+    of the first shape of that bucket, and cache the results; returns
+    bucket -> entry."""
+    sk = pcc_get_tuning()["stage_k"]
     done = {}
     for n, l in shapes:
         key = bucket(n, l, "?")[:-2]
         if key in done:
             continue
         done[key] = tune_pairs(n, l, prec, reps=reps, path=path,
-                               candidates={"stage_k": (32,),
+                               candidates={"stage_k": (sk,),
                                            "pair_mma": (1, 0),
                                            "band_rows": tuple(bands)})
     return done

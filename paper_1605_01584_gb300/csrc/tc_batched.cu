@@ -12,9 +12,9 @@
 // per matrix at run time, so one kernel serves the whole batch.
 //
 // Same roles, pipeline and bounded waits as the single-matrix kernel
-// (tc_pairs.cu), K = 32 per stage; matrices with rows longer than 1024
-// accumulate their units in chunks as that kernel does (tc_common.cuh).  With the pair
-// form (pcc_set_pair_mma, the default) the plan hands whole super-tiles to
+// (tc_pairs.cu), K = 32 or 64 per stage (the stage_k knob); matrices with
+// rows longer than 1024 accumulate their units in chunks as that kernel does
+// (tc_common.cuh).  With the pair form (pcc_set_pair_mma, the default) the plan hands whole super-tiles to
 // CTA pairs, which run one 2-SM MMA per tile (M = 256, each CTA loading its
 // 128 A rows and 128 of the B rows, as in tc_pairs.cu); otherwise single
 // CTAs take units.
@@ -35,16 +35,17 @@
 namespace pcc {
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kKB = 32, kUK = 16;
+constexpr int kBM = 128, kBN = 256, kUK = 16;
 constexpr int kThreads = 320, kEpiWarps = 8;
-constexpr int kTileA = kBM * kKB * 2;            // 8 KB
 constexpr int kEpiBytes = kEpiWarps * 32 * kStagePad * 4;
-// PAIR: each CTA holds 128 of the 256 B rows, so six smaller stages
-template <bool PAIR>
+// KB = K per stage (32 or 64, the stage_k knob); PAIR: each CTA holds 128
+// of the 256 B rows, so its stages are a third smaller
+template <bool PAIR, int KB>
 struct BCfg {
-  static constexpr int kTileB = (PAIR ? kBM : kBN) * kKB * 2;
+  static constexpr int kTileA = kBM * KB * 2;
+  static constexpr int kTileB = (PAIR ? kBM : kBN) * KB * 2;
   static constexpr int kStageBytes = 2 * (kTileA + kTileB);  // 3 products
-  static constexpr int kStages = PAIR ? 6 : 4;
+  static constexpr int kStages = (4 * 49152) / kStageBytes;
   static constexpr int kBarBytes = 512;
   static constexpr int kSmemBytes =
       1024 + kStages * kStageBytes + kEpiBytes + kBarBytes;
@@ -80,10 +81,11 @@ struct BatchParams {
 constexpr int kItemShift = 40;
 constexpr uint64_t kItemMask = (1ull << kItemShift) - 1;
 
-template <bool PAIR>
+template <bool PAIR, int KB>
 __global__ void __launch_bounds__(kThreads, 1)
     k_pairs_tc_batched(const BatchParams p) {
-  using C = BCfg<PAIR>;
+  using C = BCfg<PAIR, KB>;
+  constexpr int kTileA = C::kTileA;
   constexpr int kTileB = C::kTileB;
   constexpr int kStageBytes = C::kStageBytes;
   constexpr int kStages = C::kStages;
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int kc = kb * kKB;
+          const int kc = kb * KB;
           if constexpr (PAIR) {
             // each CTA: its 128 A rows and 128 of the B rows; both CTAs'
             // bytes count on the even CTA's barrier
@@ -250,8 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(acc * kBN);
-          const int kb0 = chunk_begin<kKB>(nkb, nch, c);
-          const int kb1 = chunk_begin<kKB>(nkb, nch, c + 1);
+          const int kb0 = chunk_begin<KB>(nkb, nch, c);
+          const int kb1 = chunk_begin<KB>(nkb, nch, c + 1);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&full[stage], phase, w)) {
               ok = false;
@@ -263,10 +265,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t aL = smem_u32(sA_lo(stage));
             const uint32_t bL = smem_u32(sB_lo(stage));
 #pragma unroll
-            for (int ks = 0; ks < kKB / kUK; ++ks) {
+            for (int ks = 0; ks < KB / kUK; ++ks) {
               const uint32_t off = ks * kUK * 2;
-              const uint64_t dAH = kmajor_desc<64>(aH + off);
-              const uint64_t dBH = kmajor_desc<64>(bH + off);
+              const uint64_t dAH = kmajor_desc<2 * KB>(aH + off);
+              const uint64_t dBH = kmajor_desc<2 * KB>(bH + off);
               auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
                 if constexpr (PAIR)
                   umma_f16_pair(d_tmem, a, b, idesc, acc_in);
@@ -275,10 +277,10 @@ __global__ void __launch_bounds__(kThreads, 1)
               };
               mma(dAH, dBH, (kb == kb0 && ks == 0) ? 0u : 1u);
               if (nprod >= 3) {
-                mma(dAH, kmajor_desc<64>(bL + off), 1u);
-                mma(kmajor_desc<64>(aL + off), dBH, 1u);
+                mma(dAH, kmajor_desc<2 * KB>(bL + off), 1u);
+                mma(kmajor_desc<2 * KB>(aL + off), dBH, 1u);
                 if (nprod == 4)
-                  mma(kmajor_desc<64>(aL + off), kmajor_desc<64>(bL + off),
+                  mma(kmajor_desc<2 * KB>(aL + off), kmajor_desc<2 * KB>(bL + off),
                       1u);
               }
             }
@@ -395,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // either 1-SM or 2-SM MMAs, never both).
 struct Launch {
   bool pair = false;     // items are tiles for CTA pairs (2-SM MMA)
+  int kb = 32;           // K per stage
   int grid = 0;          // CTAs
   void* dmem = nullptr;  // descs | cta_off | items
   MatDesc* d_descs = nullptr;
@@ -409,6 +412,7 @@ struct Plan {
   std::vector<int64_t> sig;
   double cost_c0 = 0, cost_c1 = 0;
   int64_t one_acc_l = 0, chunk_l = 0;
+  int stage_k = 32;
   int device = -1;
   Launch L[2];  // 2-SM pair matrices, then single-CTA matrices
   int nlaunch = 0;
@@ -426,12 +430,13 @@ void free_plan(Plan* P) {
 }
 
 // CTA pairs of the pair form that can be resident at once
+template <int KB>
 int pair_workers(int device) {
   static int mc_of[kDeviceSlots] = {};
   int& mc = mc_of[device_slot(device)];
   if (mc == 0) {
-    auto fn = k_pairs_tc_batched<true>;
-    const int smem = BCfg<true>::kSmemBytes;
+    auto fn = k_pairs_tc_batched<true, KB>;
+    const int smem = BCfg<true, KB>::kSmemBytes;
     int v = 0;
     if (ensure_func_smem(reinterpret_cast<const void*>(fn), smem) ==
         cudaSuccess) {
@@ -459,7 +464,7 @@ int pair_workers(int device) {
 // longest first, each to the least-loaded worker, then each worker's list
 // in (matrix, unit) order.
 bool build_launch(Plan* P, Launch* L, const std::vector<int>& mats,
-                  bool pair) {
+                  bool pair, int KB) {
   const int B = (int)mats.size();
   const int sms = num_sms(P->device);
   std::vector<MatDesc> descs(B);
@@ -473,11 +478,12 @@ bool build_launch(Plan* P, Launch* L, const std::vector<int>& mats,
     const pcc_zmat* Z = P->zs[b];
     MatDesc& d = descs[lb];
     memset(&d, 0, sizeof(d));
-    d.tm_hi = Z->tm_hi32;
-    d.tm_lo = Z->tm_lo32;
+    // K = 64 stages: box 64 x 128, 128-byte swizzle; K = 32: 32 x 128, 64-B
+    d.tm_hi = KB == 64 ? Z->tm_hi : Z->tm_hi32;
+    d.tm_lo = KB == 64 ? Z->tm_lo : Z->tm_lo32;
     d.n = Z->n;
     d.m = tc_super_count(Z->n);
-    d.nkb = (int)(Z->lpad / kKB);
+    d.nkb = (int)(Z->lpad / KB);
     d.nprod = Z->prec == PCC_PREC_BF16X1   ? 1
               : Z->prec == PCC_PREC_BF16X4 ? 4
                                            : 3;
@@ -489,9 +495,11 @@ bool build_launch(Plan* P, Launch* L, const std::vector<int>& mats,
     d.scale = (float)ldexp(1.0, -2 * Z->scale_exp);
     d.flags = Z->flags;
     d.R = P->rs[b];
-    // a unit's cost; a tile of the pair form costs the same (its two
-    // halves run side by side on the pair)
-    const double cost = P->cost_c0 + P->cost_c1 * d.nkb * d.nprod;
+    // a unit's cost (c1 per 32 samples and product, whatever the stage
+    // size); a tile of the pair form costs the same (its two halves run
+    // side by side on the pair)
+    const double cost =
+        P->cost_c0 + P->cost_c1 * (double)(Z->lpad / 32) * d.nprod;
     if (pair) {
       const int64_t nt = tc_num_tiles(Z->n);
       for (int64_t t = 0; t < nt; ++t)
@@ -510,7 +518,9 @@ bool build_launch(Plan* P, Launch* L, const std::vector<int>& mats,
   }
   const int64_t total = (int64_t)units.size();
   // workers: CTAs, or CTA pairs in the pair form
-  const int64_t nw = pair ? pair_workers(P->device) : sms;
+  const int64_t nw = pair ? (KB == 64 ? pair_workers<64>(P->device)
+                                      : pair_workers<32>(P->device))
+                         : sms;
   int grid = (int)std::min<int64_t>(nw, std::max<int64_t>(total, 1));
   std::stable_sort(units.begin(), units.end(),
                    [](const U& a, const U& b) { return a.cost > b.cost; });
@@ -559,6 +569,7 @@ bool build_launch(Plan* P, Launch* L, const std::vector<int>& mats,
     return false;
   }
   L->pair = pair;
+  L->kb = KB;
   L->grid = pair ? 2 * grid : grid;
   return true;
 }
@@ -569,19 +580,22 @@ bool build_plan(Plan* P) {
     by_form[P->sig[kSig * b + 4] ? 0 : 1].push_back(b);
   for (int f = 0; f < 2; ++f) {
     if (by_form[f].empty()) continue;
-    if (!build_launch(P, &P->L[P->nlaunch], by_form[f], f == 0)) return false;
+    if (!build_launch(P, &P->L[P->nlaunch], by_form[f], f == 0,
+                      P->stage_k))
+      return false;
     ++P->nlaunch;
   }
   return true;
 }
 
-cudaError_t launch_one(const Launch& L, const BatchParams& bp,
-                       cudaStream_t s) {
-  if (L.pair) {
-    auto fn = k_pairs_tc_batched<true>;
-    const int smem = BCfg<true>::kSmemBytes;
-    cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
-    if (e != cudaSuccess) return e;
+template <bool PAIR, int KB>
+cudaError_t launch_form(const Launch& L, const BatchParams& bp,
+                        cudaStream_t s) {
+  auto fn = k_pairs_tc_batched<PAIR, KB>;
+  const int smem = BCfg<PAIR, KB>::kSmemBytes;
+  cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  if constexpr (PAIR) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -598,12 +612,17 @@ cudaError_t launch_one(const Launch& L, const BatchParams& bp,
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  auto fn = k_pairs_tc_batched<false>;
-  const int smem = BCfg<false>::kSmemBytes;
-  cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
-  if (e != cudaSuccess) return e;
   fn<<<L.grid, kThreads, smem, s>>>(bp);
   return cudaGetLastError();
+}
+
+cudaError_t launch_one(const Launch& L, const BatchParams& bp,
+                       cudaStream_t s) {
+  if (L.pair)
+    return L.kb == 64 ? launch_form<true, 64>(L, bp, s)
+                      : launch_form<true, 32>(L, bp, s);
+  return L.kb == 64 ? launch_form<false, 64>(L, bp, s)
+                    : launch_form<false, 32>(L, bp, s);
 }
 
 }  // namespace
@@ -631,6 +650,7 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
     for (Plan* q : g_plans) {
       if ((int)q->zs.size() != B || q->device != dev) continue;
       bool same = q->cost_c0 == tn.cost_c0 && q->cost_c1 == tn.cost_c1 &&
+                  q->stage_k == tn.stage_k &&
                   q->one_acc_l == tn.one_acc_l && q->chunk_l == tn.chunk_l &&
                   q->sig == sig;
       for (int b = 0; b < B && same; ++b)
@@ -649,6 +669,7 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
       P->cost_c1 = tn.cost_c1;
       P->one_acc_l = tn.one_acc_l;
       P->chunk_l = tn.chunk_l;
+      P->stage_k = tn.stage_k;
       P->device = dev;
       if (!build_plan(P)) {
         free_plan(P);

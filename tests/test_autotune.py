@@ -67,7 +67,7 @@ def test_lookup_skips_unusable_entries():
     assert autotune.lookup(65536, 512, "bf16x3", {}) is None
 
 
-def test_lookup_batched_takes_the_best_k32_run():
+def test_lookup_batched_takes_the_best_run_of_the_stage_size():
     runs = [{"stage_k": 64, "cluster": 1, "pair_mma": 0, "band_rows": 8,
              "ms": 1.0},
             {"stage_k": 32, "cluster": 1, "pair_mma": 0, "band_rows": 16,
@@ -75,9 +75,11 @@ def test_lookup_batched_takes_the_best_k32_run():
             {"stage_k": 32, "cluster": 2, "pair_mma": 1, "band_rows": 32,
              "ms": 1.1}]
     cache = {"n4096_l512_fp16x3s": {"best": runs[0], "all": runs}}
-    assert autotune.lookup_batched(4096, 500, "fp16x3s", cache) == (1, 32)
+    lb = autotune.lookup_batched
+    assert lb(4096, 500, "fp16x3s", cache, stage_k=32) == (1, 32)
+    assert lb(4096, 500, "fp16x3s", cache, stage_k=64) == (0, 8)
     # nearest n in the same (padded l, form) bucket
-    assert autotune.lookup_batched(3000, 512, "fp16x3s", cache) == (1, 32)
-    assert autotune.lookup_batched(4096, 700, "fp16x3s", cache) is None
+    assert lb(3000, 512, "fp16x3s", cache, stage_k=32) == (1, 32)
+    assert lb(4096, 700, "fp16x3s", cache, stage_k=32) is None
     cache["n4096_l512_fp16x3s"]["all"] = runs[:1]  # no K = 32 run
-    assert autotune.lookup_batched(4096, 512, "fp16x3s", cache) is None
+    assert lb(4096, 512, "fp16x3s", cache, stage_k=32) is None

@@ -272,8 +272,8 @@ def _single(pcc, Z, R, pair, band):
     torch = _torch()
     old = pcc.pcc_get_tuning()
     try:
-        pcc.pcc_set_tuning(stage_k=32, cluster=2 if pair else 1,
-                           band_rows=band, pair_mma=pair)
+        pcc.pcc_set_tuning(cluster=2 if pair else 1, band_rows=band,
+                           pair_mma=pair)
         out = torch.full_like(R, 7.0)
         pcc.pcc_allpairs_upper(Z, out)
         assert pcc.pcc_sync_status(Z) == 0
@@ -322,23 +322,24 @@ def test_batched_per_matrix_choices(pcc_gpu):
 
 def test_batched_default_consults_the_tune_cache(pcc_gpu):
     """With a tune cache holding entries for some shapes, the default call
-    gives those matrices the cached best (K = 32) choice and the rest the
-    current knobs."""
+    gives those matrices the cached best choice at the batched kernel's
+    stage size and the rest the current knobs."""
     pcc = pcc_gpu
     from paper_1605_01584_gb300 import autotune
     Xs, Zs, Rs = _setup(pcc, TUNED, seed0=960)
+    t = pcc.pcc_get_tuning()
+    sk, other = t["stage_k"], 96 - t["stage_k"]  # 32 <-> 64
     cache = {}
     for (n, l, prec), (pair, band) in zip(TUNED[:2], [(0, 4), (1, 16)]):
         cache[autotune.bucket(n, l, prec)] = {
-            "best": {"stage_k": 64, "cluster": 1, "band_rows": 8,
+            "best": {"stage_k": other, "cluster": 1, "band_rows": 8,
                      "pair_mma": 0, "ms": 0.5},
-            "all": [{"stage_k": 64, "cluster": 1, "pair_mma": 0,
+            "all": [{"stage_k": other, "cluster": 1, "pair_mma": 0,
                      "band_rows": 8, "ms": 0.5},
-                    {"stage_k": 32, "cluster": 2 if pair else 1,
+                    {"stage_k": sk, "cluster": 2 if pair else 1,
                      "pair_mma": pair, "band_rows": band, "ms": 0.6},
-                    {"stage_k": 32, "cluster": 1, "pair_mma": 0,
+                    {"stage_k": sk, "cluster": 1, "pair_mma": 0,
                      "band_rows": 64, "ms": 0.9}]}
-    t = pcc.pcc_get_tuning()
     default = (1 if t["pair_mma"] and t["cluster"] == 2 else 0,
                t["band_rows"])
     used = pcc.pcc_allpairs_upper_batched(Zs, Rs, cache=cache)
