@@ -44,12 +44,9 @@ namespace pcc {
 namespace {
 
 constexpr int kPT = 128;      // tile side (MMA M; N = 128 per permutation)
-constexpr int kPK = 32;       // K per stage (64-B swizzle rows)
 constexpr int kPUK = 16;
 constexpr int kPThreads = 320;
 constexpr int kPEpiWarps = 8;
-constexpr int kPTile = kPT * kPK * 2;        // 8 KB: 128 rows x 32 (16-bit)
-constexpr int kPBHalf = 2 * kPTile;          // B hi (or lo): 256 rows, 16 KB
 constexpr int kPAcc = 2 * kPT;               // TMEM columns per accumulator
 constexpr int kPMaxResidentK = 256;          // resident A up to lpad 256
 constexpr int kPSmemBudget = 232448;
@@ -101,15 +98,18 @@ struct PermParams {
   uint64_t wait_ns;
 };
 
-// PAIR: a CTA pair runs one 2-SM MMA (M = 256: the two CTAs' tiles); each
-// CTA holds the 128 B rows of one permutation, so its B stages are half as
-// large.
-template <bool RESA, bool PAIR = false>
+// KP = K per stage: 32 (64-byte swizzle rows) or, in the pair form, 64
+// (128-byte rows: half as many copies and stage hand-offs).  PAIR: a CTA
+// pair runs one 2-SM MMA (M = 256: the two CTAs' tiles); each CTA holds the
+// 128 B rows of one permutation, so its B stages are half as large.
+template <bool RESA, bool PAIR, int KP>
 struct PCfg {
-  // resident A: nkb blocks x (hi + lo) tiles, at most kPMaxResidentK / kPK
-  static constexpr int kABytes = RESA ? (kPMaxResidentK / kPK) * 2 * kPTile : 0;
+  static constexpr int kPTile = kPT * KP * 2;  // 128 rows x KP (16-bit)
+  // resident A: nkb blocks x (hi + lo) tiles, up to kPMaxResidentK samples
+  static constexpr int kABytes =
+      RESA ? (kPMaxResidentK / KP) * 2 * kPTile : 0;
   // B hi (or lo) rows of a stage: 256 (two permutations), PAIR: 128 (one)
-  static constexpr int kBHalf = PAIR ? kPTile : kPBHalf;
+  static constexpr int kBHalf = PAIR ? kPTile : 2 * kPTile;
   // stage: [B hi | B lo], streamed A in front of them
   static constexpr int kStageBytes =
       RESA ? 2 * kBHalf : 2 * kPTile + 2 * kBHalf;
@@ -260,14 +260,15 @@ cudaError_t launch_gather(dim3 g, size_t gsmem, cudaStream_t s,
   return go(k_perm_gather<0, 1>);
 }
 
-template <bool BF16, bool RESA, bool PAIR>
+template <bool BF16, bool RESA, bool PAIR, int KP>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_perm_tc(const __grid_constant__ CUtensorMap tz_hi,
               const __grid_constant__ CUtensorMap tz_lo,
               const __grid_constant__ CUtensorMap tp_hi,
               const __grid_constant__ CUtensorMap tp_lo, const PermParams p) {
-  using C = PCfg<RESA, PAIR>;
+  using C = PCfg<RESA, PAIR, KP>;
   constexpr int S = C::kStages;
+  constexpr int kPTile = C::kPTile;
   // N = 128: r_obs and a lone last permutation; N = 256: two permutations.
   // PAIR: always M = 256 (both CTAs' tiles) and N = 256 (one permutation's
   // 128 B rows from each CTA; r_obs and a lone permutation repeat theirs)
@@ -403,17 +404,17 @@ __global__ void __launch_bounds__(kPThreads, 1)
               mbar_arrive_expect_tx(afull, (uint32_t)(2 * p.nkb * 2 * kPTile));
             const uint32_t ab = cluster_addr(afull, 0);
             for (int kb = 0; kb < p.nkb; ++kb) {
-              tma_load_2d_pair(sA_hi(0, kb), &tz_hi, ab, kb * kPK, (int)row0,
+              tma_load_2d_pair(sA_hi(0, kb), &tz_hi, ab, kb * KP, (int)row0,
                                pol);
-              tma_load_2d_pair(sA_lo(0, kb), &tz_lo, ab, kb * kPK, (int)row0,
+              tma_load_2d_pair(sA_lo(0, kb), &tz_lo, ab, kb * KP, (int)row0,
                                pol);
             }
           } else {
             mbar_arrive_expect_tx(afull, (uint32_t)(p.nkb * 2 * kPTile));
             for (int kb = 0; kb < p.nkb; ++kb) {
-              tma_load_2d_hint(sA_hi(0, kb), &tz_hi, afull, kb * kPK,
+              tma_load_2d_hint(sA_hi(0, kb), &tz_hi, afull, kb * KP,
                                (int)row0, pol);
-              tma_load_2d_hint(sA_lo(0, kb), &tz_lo, afull, kb * kPK,
+              tma_load_2d_hint(sA_lo(0, kb), &tz_lo, afull, kb * KP,
                                (int)row0, pol);
             }
           }
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
               ok = false;
               break;
             }
-            const int kc = kb * kPK;
+            const int kc = kb * KP;
             if constexpr (PAIR) {
               // each CTA: (its streamed A and) the 128 B rows of one
               // permutation, the even CTA k, the odd CTA k + 1 (r_obs and a
@@ -534,12 +535,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
             const uint32_t bH = smem_u32(sB_hi(stage));
             const uint32_t bL = smem_u32(sB_lo(stage));
 #pragma unroll
-            for (int ks = 0; ks < kPK / kPUK; ++ks) {
+            for (int ks = 0; ks < KP / kPUK; ++ks) {
               const uint32_t off = ks * kPUK * 2;
-              const uint64_t dAH = kmajor_desc<64>(aH + off);
-              const uint64_t dBH = kmajor_desc<64>(bH + off);
-              const uint64_t dAL = kmajor_desc<64>(aL + off);
-              const uint64_t dBL = kmajor_desc<64>(bL + off);
+              const uint64_t dAH = kmajor_desc<2 * KP>(aH + off);
+              const uint64_t dBH = kmajor_desc<2 * KP>(bH + off);
+              const uint64_t dAL = kmajor_desc<2 * KP>(aL + off);
+              const uint64_t dBL = kmajor_desc<2 * KP>(bL + off);
               auto mma = [&](uint64_t a, uint64_t b, uint32_t acc_in) {
                 if constexpr (PAIR)
                   umma_f16_pair(d_tmem, a, b, idesc, acc_in);
@@ -678,12 +679,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
   }
 }
 
-template <bool BF16, bool RESA, bool PAIR>
+template <bool BF16, bool RESA, bool PAIR, int KP>
 cudaError_t launch_perm_kernel(const pcc_zmat* Z, const CUtensorMap& ph,
                                const CUtensorMap& pl, const PermParams& p,
                                cudaStream_t s) {
-  auto fn = k_perm_tc<BF16, RESA, PAIR>;
-  const int smem = PCfg<RESA, PAIR>::kSmemBytes;
+  auto fn = k_perm_tc<BF16, RESA, PAIR, KP>;
+  const int smem = PCfg<RESA, PAIR, KP>::kSmemBytes;
+  // Z's maps with the stage's box: 64 x 128 (128-B swizzle) or 32 x 128
+  const CUtensorMap& zh = KP == 64 ? Z->tm_hi : Z->tm_hi32;
+  const CUtensorMap& zl = KP == 64 ? Z->tm_lo : Z->tm_lo32;
   cudaError_t e = ensure_func_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   if constexpr (PAIR) {
@@ -712,14 +716,13 @@ cudaError_t launch_perm_kernel(const pcc_zmat* Z, const CUtensorMap& ph,
     }
     const int64_t ncl = p.items < max_clusters ? p.items : max_clusters;
     cfg.gridDim = dim3((unsigned)(2 * ncl), 1, 1);
-    e = cudaLaunchKernelEx(&cfg, fn, Z->tm_hi32, Z->tm_lo32, ph, pl, p);
+    e = cudaLaunchKernelEx(&cfg, fn, zh, zl, ph, pl, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
   int64_t grid = num_sms(Z->device);
   if (p.items < grid) grid = p.items;
-  fn<<<(unsigned)grid, kPThreads, smem, s>>>(Z->tm_hi32, Z->tm_lo32, ph, pl,
-                                             p);
+  fn<<<(unsigned)grid, kPThreads, smem, s>>>(zh, zl, ph, pl, p);
   return cudaGetLastError();
 }
 
@@ -765,6 +768,9 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
   const int64_t m = (n + kPT - 1) / kPT;
   // the CTA-pair form takes the tiles of a column two at a time
   const bool pair = tc_tuning().pair_mma != 0 && m >= 2;
+  // the pair form follows the stage_k knob; single CTAs keep K = 32 (a
+  // 64-sample stage next to the resident A tile leaves room for one stage)
+  const int KP = pair && tc_tuning().stage_k == 64 ? 64 : 32;
   const int64_t tiles = pair ? col_pairs_before(m) : m * (m + 1) / 2;
   const int sms = num_sms(Z->device);
   if ((size_t)lpad * 4 + (size_t)kGatherWarps * 4 * lpad > 200 * 1024)
@@ -784,8 +790,8 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                       lpad, kb0, rpb, wh, wl, Z->status);
     if (e != cudaSuccess) return cuda_status(e);
     CUtensorMap ph, pl;
-    if (!encode_tmap_3d_u16(&ph, wh, kbatch, n, lpad, kPT, kPK, bf16) ||
-        !encode_tmap_3d_u16(&pl, wl, kbatch, n, lpad, kPT, kPK, bf16))
+    if (!encode_tmap_3d_u16(&ph, wh, kbatch, n, lpad, kPT, KP, bf16) ||
+        !encode_tmap_3d_u16(&pl, wl, kbatch, n, lpad, kPT, KP, bf16))
       return PCC_ERR_CUDA;
     // chunks of about kPermChunk permutations: short enough that the
     // permuted panels in flight fit in L2, long enough that r_obs (one
@@ -804,26 +810,39 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     p.nchunks = (int)nchunks;
     p.chunk = (int)chunk;
     p.kbatch = (int)kbatch;
-    p.nkb = (int)(lpad / kPK);
+    p.nkb = (int)(lpad / KP);
     p.lolo = Z->prec == PCC_PREC_BF16X4 ? 1 : 0;
     p.flags = Z->flags;
     p.counts = d_counts;
     p.status = Z->status;
     p.wait_ns = wait_limit_ns();
-    if (pair) {
-      if (lpad <= kPMaxResidentK)
-        e = bf16 ? launch_perm_kernel<true, true, true>(Z, ph, pl, p, s)
-                 : launch_perm_kernel<false, true, true>(Z, ph, pl, p, s);
+    const bool resa = lpad <= kPMaxResidentK;
+    if (pair && KP == 64) {
+      if (resa)
+        e = bf16 ? launch_perm_kernel<true, true, true, 64>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, true, true, 64>(Z, ph, pl, p, s);
       else
-        e = bf16 ? launch_perm_kernel<true, false, true>(Z, ph, pl, p, s)
-                 : launch_perm_kernel<false, false, true>(Z, ph, pl, p, s);
+        e = bf16 ? launch_perm_kernel<true, false, true, 64>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, false, true, 64>(Z, ph, pl, p,
+                                                              s);
+    } else if (pair) {
+      if (resa)
+        e = bf16 ? launch_perm_kernel<true, true, true, 32>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, true, true, 32>(Z, ph, pl, p, s);
+      else
+        e = bf16 ? launch_perm_kernel<true, false, true, 32>(Z, ph, pl, p, s)
+                 : launch_perm_kernel<false, false, true, 32>(Z, ph, pl, p,
+                                                              s);
     } else {
-      if (lpad <= kPMaxResidentK)
-        e = bf16 ? launch_perm_kernel<true, true, false>(Z, ph, pl, p, s)
-                 : launch_perm_kernel<false, true, false>(Z, ph, pl, p, s);
+      if (resa)
+        e = bf16
+                ? launch_perm_kernel<true, true, false, 32>(Z, ph, pl, p, s)
+                : launch_perm_kernel<false, true, false, 32>(Z, ph, pl, p, s);
       else
-        e = bf16 ? launch_perm_kernel<true, false, false>(Z, ph, pl, p, s)
-                 : launch_perm_kernel<false, false, false>(Z, ph, pl, p, s);
+        e = bf16
+                ? launch_perm_kernel<true, false, false, 32>(Z, ph, pl, p, s)
+                : launch_perm_kernel<false, false, false, 32>(Z, ph, pl, p,
+                                                              s);
     }
     if (e != cudaSuccess) return cuda_status(e);
   }
