@@ -162,6 +162,9 @@ def committed_traffic(n, l):
     scale = (n * (n - 1) / 2) / (d["n"] * (d["n"] - 1) / 2)
     if d.get("l") != l:
         return None, "captured at another l"
+    if scale == 1.0:
+        return d["dram_bytes_per_launch"], (
+            f"ncu dram read+write of one launch at this size (n={d['n']})")
     return d["dram_bytes_per_launch"] * scale, (
         f"ncu dram read+write at n={d['n']}, scaled by pairs x{scale:.2f}")
 
