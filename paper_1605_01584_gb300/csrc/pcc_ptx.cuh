@@ -37,11 +37,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar,
       : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
 // Lower the pending transaction count of the current phase of `bar` by
 // `bytes` without a copy: cancels the share of bytes a peer announced
 // but never sent (the pair form's drain after an abort).
@@ -238,10 +233,23 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
                : "memory");
 }
 
-// Arrive on an mbarrier given by its shared::cluster address (another CTA).
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+// Hand a TMEM accumulator buffer back to the MMA issuer, on a barrier of
+// this CTA (tmem_release) or, by its shared::cluster address, of the other
+// CTA of the pair (tmem_release_cluster).  The arriving thread's tcgen05.ld
+// reads have completed (tcgen05.wait::ld) and tcgen05.fence::before_thread_
+// sync orders them before the arrive; nothing the issuer does reads this
+// thread's global stores.  So the arrive is relaxed: with release semantics
+// at cluster scope it would first wait until every store the warp has in
+// flight had reached L2, which stalls the store stream of the epilogue.
+__device__ __forceinline__ void tmem_release(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_release_cluster(uint32_t addr) {
   asm volatile(
-      "mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+      "mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(
           addr)
       : "memory");
 }

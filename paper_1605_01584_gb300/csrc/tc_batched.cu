@@ -324,9 +324,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) {
         if (PAIR && crank != 0)
-          mbar_arrive_cluster(cluster_addr(&tempty[a], 0));
+          tmem_release_cluster(cluster_addr(&tempty[a], 0));
         else
-          mbar_arrive(&tempty[a]);
+          tmem_release(&tempty[a]);
       }
     };
     for (int64_t it = it0; it < it1; ++it) {

@@ -641,9 +641,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
         __syncwarp();
         if (lane == 0) {
           if (PAIR && crank != 0)  // released to the even CTA's MMA issuer
-            mbar_arrive_cluster(cluster_addr(&tempty[acc], 0));
+            tmem_release_cluster(cluster_addr(&tempty[acc], 0));
           else
-            mbar_arrive(&tempty[acc]);
+            tmem_release(&tempty[acc]);
         }
         acc ^= 1;
         if (acc == 0) aphase ^= 1u;
