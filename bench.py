@@ -618,6 +618,16 @@ def run_perm(args):
     ms_graph = _graph_timed(step, max(3, min(args.steps, 20)), 1)
     ms = ms_graph if ms_graph is not None else ms_stream
     st = pcc.pcc_sync_status(Z)
+    # the shared-memory form (no workspace): its time, and the same counts
+    ref_cnt = cnt.clone()
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(perm_workspace=0)
+        ms_smem = _timed(step, 3, 1, stream)
+        smem_equal = bool(torch.equal(cnt, ref_cnt))
+        st_smem = pcc.pcc_sync_status(Z)
+    finally:
+        pcc.pcc_set_tuning(perm_workspace=before["perm_workspace"])
     info = Z.info()
     tiles = (-(-n // 128)) * (-(-n // 128) + 1) // 2
     exec_flops = FORMS[info["prec"]][1] * 2 * 128 * 128 * info["lpad"] * tiles * (P + 1)
@@ -646,7 +656,13 @@ def run_perm(args):
                        "r_obs pass per 128 x 128 tile; the kernel also "
                        "repeats r_obs per chunk of permutations and pads "
                        "lone tiles in the pair form (about 5% more tensor "
-                       "work, not counted)"}}
+                       "work, not counted)"},
+           # the form that allocates nothing (pcc_set_perm_workspace(0)),
+           # stream-launched, 3 steps
+           "shared_memory_form": {
+               "ms_per_step": ms_smem, "counts_equal": smem_equal,
+               "status": st_smem,
+               "value": n * (n - 1) / 2 * l * P / (ms_smem / 1e3) / 1e9}}
     print(json.dumps(out), flush=True)
     return 0
 

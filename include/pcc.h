@@ -294,10 +294,22 @@ pcc_status pcc_edges_copy_host(const pcc_edge *edges, const uint64_t *d_count,
  * z_j[pi_k[s]] (only the second row of a pair is permuted); d_counts[J(i,j)]
  * is INCREASED by #{k : |r_k(i,j)| >= |r(i,j)|}.  Counting a range and
  * adding lets a long test be split or resumed.
- *   d_perms   device int32, P x l, row k a permutation of 0..l-1 (not
- *             checked on the device).
+ *   d_perms   device int32, P x l, row k a permutation of 0..l-1.  Each
+ *             index is checked on the device: one outside [0, l) is read as
+ *             sample 0 and recorded as PCC_ERR_INVALID_ARG in Z's status
+ *             (pcc_sync_status).  Whether a row is a permutation is not
+ *             checked.
  *   d_counts  device uint32, n(n-1)/2, packed like R.
- * The first call on a Z allocates a work buffer kept in Z.
+ * Two forms, with the same counts:
+ *   - the workspace form (the default): the permuted rows of a batch of
+ *     permutations are first written to a work buffer, allocated by the
+ *     first such call on a Z and kept in Z (4.2 GB for 1,000 permutations
+ *     of a 4,096 x 256 matrix; smaller budgets run in batches);
+ *   - the shared-memory form (pcc_set_perm_workspace(0), CTA pairs, rows of
+ *     up to 256 padded samples): each CTA keeps 64 of the column tile's
+ *     rows z_j resident in shared memory and builds every permuted operand
+ *     there; no device memory is allocated, at about 2.5 times the
+ *     workspace form's time (shared-memory bandwidth).
  * Errors: PCC_ERR_INVALID_ARG for a bad range, NULL pointers or a non
  * tensor-core Z. */
 pcc_status pcc_perm_test(const pcc_zmat *Z, const int32_t *d_perms,
@@ -380,7 +392,9 @@ pcc_status pcc_sync_status(pcc_zmat *Z, void *stream);
  *              pair form, whose stages are a third smaller) or 64 (2; 3 in
  *              the pair form; the default, PCC_TC_BK=32 in the environment
  *              selects 32 when the library loads).  The batched kernel
- *              follows it too; the permutation kernel always uses K = 32.
+ *              follows it too.  The permutation test's workspace form
+ *              follows it with CTA pairs (single CTAs keep 32); its
+ *              shared-memory form always stages 32.
  *   cluster    2 = CTA pairs running one 2-SM MMA (while
  *              pcc_set_pair_mma is on), 1 = independent CTAs.
  *   band_rows  super-tile rows per band of the pair schedule (rows of a
@@ -412,6 +426,17 @@ pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
  * (a GB300 execution choice). */
 pcc_status pcc_set_pair_mma(int32_t on);
 int32_t pcc_get_pair_mma(void);
+
+/* The form of pcc_perm_test.  on = 1 (the default; PCC_PERM_WORKSPACE=0 in
+ * the environment selects 0 when the library loads): every call gathers
+ * the permuted rows into a work buffer first; 0: CTA pairs permute the
+ * column rows in shared memory wherever rows fit (padded length <= 256 and
+ * pcc_set_pair_mma on), allocating nothing.  Affects later calls only; the
+ * counts are the same.
+ * Errors: PCC_ERR_INVALID_ARG unless on is 0 or 1.  The paper has no
+ * counterpart (a GB300 execution choice). */
+pcc_status pcc_set_perm_workspace(int32_t on);
+int32_t pcc_get_perm_workspace(void);
 
 /* Current knob values (any pointer may be NULL). */
 pcc_status pcc_get_tuning(int32_t *stage_k, int32_t *cluster,

@@ -122,6 +122,8 @@ def load(path: str | None = None):
         "pcc_set_pair_mma": (_ST, [_I32]),
         "pcc_measure_fp32_fma": (_ST, [_P, _P]),
         "pcc_get_pair_mma": (_I32, []),
+        "pcc_set_perm_workspace": (_ST, [_I32]),
+        "pcc_get_perm_workspace": (_I32, []),
         "pcc_num_pairs": (_I64, [_I64]),
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
         "pcc_pair_coords": (_ST, [_I64, _I64, _P, _P]),
@@ -514,14 +516,20 @@ def pcc_debug_drop_loads(enable):
 
 
 def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,
-                   cost_c1=0.0, pair_mma=None):
-    """Zeros (and pair_mma=None) keep a value; pair_mma 1/0 selects CTA
-    pairs running one 2-SM MMA or independent CTAs (pcc_set_pair_mma)."""
+                   cost_c1=0.0, pair_mma=None, perm_workspace=None):
+    """Zeros (and None) keep a value; pair_mma 1/0 selects CTA pairs running
+    one 2-SM MMA or independent CTAs (pcc_set_pair_mma); perm_workspace
+    1 (the default) runs the permutation test through a workspace of
+    permuted rows, 0 lets CTA pairs permute them in shared memory where
+    rows fit, allocating nothing (pcc_set_perm_workspace)."""
     _check(load().pcc_set_tuning(int(stage_k), int(cluster), int(band_rows),
                                  float(cost_c0), float(cost_c1)),
            "pcc_set_tuning")
     if pair_mma is not None:
         _check(load().pcc_set_pair_mma(int(pair_mma)), "pcc_set_pair_mma")
+    if perm_workspace is not None:
+        _check(load().pcc_set_perm_workspace(int(perm_workspace)),
+               "pcc_set_perm_workspace")
 
 
 def pcc_measure_fp32_fma(stream=None) -> float:
@@ -540,7 +548,8 @@ def pcc_get_tuning() -> dict:
                                  ctypes.byref(c1)), "pcc_get_tuning")
     return dict(stage_k=k.value, cluster=c.value, band_rows=b.value,
                 cost_c0=c0.value, cost_c1=c1.value,
-                pair_mma=int(load().pcc_get_pair_mma()))
+                pair_mma=int(load().pcc_get_pair_mma()),
+                perm_workspace=int(load().pcc_get_perm_workspace()))
 
 
 def pcc_num_pairs(n: int) -> int:

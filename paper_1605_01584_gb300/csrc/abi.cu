@@ -114,6 +114,10 @@ TcTuning g_tune = [] {
   t.band = (v >= 1 && v <= 4096) ? v : 32;
   t.cost_c0 = 3000.0;
   t.cost_c1 = 260.0;
+  // the workspace form of the permutation test is the faster one; the
+  // shared-memory form is chosen with PCC_PERM_WORKSPACE=0
+  e = getenv("PCC_PERM_WORKSPACE");
+  t.perm_workspace = (e && atoi(e) == 0) ? 0 : 1;
   e = getenv("PCC_TC_ONEACC");
   const int oa = e ? atoi(e) : 0;
   t.one_acc_l = oa >= 64 ? oa : 1024;
@@ -669,6 +673,16 @@ pcc_status pcc_set_pair_mma(int32_t on) {
 }
 
 int32_t pcc_get_pair_mma(void) { return tc_tuning().pair_mma; }
+
+pcc_status pcc_set_perm_workspace(int32_t on) {
+  if (on != 0 && on != 1) return PCC_ERR_INVALID_ARG;
+  TcTuning t = tc_tuning();
+  t.perm_workspace = on;
+  tc_set_tuning(t);
+  return PCC_OK;
+}
+
+int32_t pcc_get_perm_workspace(void) { return tc_tuning().perm_workspace; }
 
 pcc_status pcc_get_tuning(int32_t* stage_k, int32_t* cluster,
                           int32_t* band_rows, double* cost_c0,

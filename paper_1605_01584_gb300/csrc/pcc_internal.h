@@ -84,6 +84,10 @@ struct TcTuning {
   double cost_c1;    // batched plan: cycles per K block and product
   int64_t one_acc_l;  // padded rows up to this length use one accumulator
   int64_t chunk_l;    // longer rows: accumulator chunks of at most this
+  int perm_workspace;  // 1 (default): the permutation test gathers
+                       // permuted rows into a workspace; 0: CTA pairs
+                       // permute in shared memory where rows fit
+                       // (lpad <= 256)
 };
 TcTuning tc_tuning();
 void tc_set_tuning(const TcTuning& t);
@@ -162,5 +166,11 @@ pcc_status allpairs_batched(const pcc_zmat* const* Zs, int32_t B,
 pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                      int32_t k0, int32_t k1, uint32_t* d_counts,
                      cudaStream_t s);
+// K6 on CTA pairs that permute the column rows in shared memory
+// (tc_perm_smem.cu): for rows of up to 256 padded samples, when the pair
+// form is on and the shared-memory form is selected (perm_workspace 0).
+bool perm_smem_applies(const pcc_zmat* Z);
+pcc_status perm_test_smem(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
+                          int32_t k1, uint32_t* d_counts, cudaStream_t s);
 
 }  // namespace pcc

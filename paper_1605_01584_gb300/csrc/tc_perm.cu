@@ -39,17 +39,12 @@
 #include "pcc_ptx.cuh"
 #include "pcc_sched.h"
 #include "tc_common.cuh"
+#include "tc_perm_common.cuh"
 
 namespace pcc {
 namespace {
 
-constexpr int kPT = 128;      // tile side (MMA M; N = 128 per permutation)
-constexpr int kPUK = 16;
 constexpr int kPThreads = 320;
-constexpr int kPEpiWarps = 8;
-constexpr int kPAcc = 2 * kPT;               // TMEM columns per accumulator
-constexpr int kPMaxResidentK = 256;          // resident A up to lpad 256
-constexpr int kPSmemBudget = 232448;
 constexpr int64_t kPermChunk = 48;           // permutations per work item
 
 // column-major numbering of the upper triangle of tiles (diagonal in):
@@ -63,24 +58,6 @@ __device__ __forceinline__ void col_tri_coords(int64_t t, int64_t* y,
   while ((xx + 1) * (xx + 2) / 2 <= t) ++xx;
   *x = xx;
   *y = t - xx * (xx + 1) / 2;
-}
-
-// PAIR items: the tiles of column x of the triangle taken two by two, rows
-// (2r, 2r+1); column x holds floor((x+2)/2) pairs (the last one alone when
-// x is even) and Q(x) = floor((x+1)/2) * floor((x+2)/2) pairs come before
-// it.  The closed-form estimate is corrected by exact integer tests.
-__host__ __device__ __forceinline__ int64_t col_pairs_before(int64_t x) {
-  return ((x + 1) / 2) * ((x + 2) / 2);
-}
-
-__device__ __forceinline__ void col_pair_coords(int64_t t, int64_t* r,
-                                                int64_t* x) {
-  int64_t xx = (int64_t)(2.0 * sqrt((double)t));
-  if (xx < 0) xx = 0;
-  while (xx > 0 && col_pairs_before(xx) > t) --xx;
-  while (col_pairs_before(xx + 1) <= t) ++xx;
-  *x = xx;
-  *r = t - col_pairs_before(xx);
 }
 
 struct PermParams {
@@ -743,6 +720,9 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
   if (Z->prec != PCC_PREC_BF16X3 && Z->prec != PCC_PREC_FP16X3S &&
       Z->prec != PCC_PREC_BF16X4)
     return PCC_ERR_INVALID_ARG;
+  // CTA pairs permute in shared memory where the rows fit: no workspace
+  if (perm_smem_applies(Z))
+    return perm_test_smem(Z, d_perms, k0, k1, d_counts, s);
   const int64_t n = Z->n, lpad = Z->lpad;
   const size_t per_k = (size_t)n * (size_t)lpad * 2 * 2;  // hi + lo
   int64_t kbmax = (int64_t)(perm_ws_budget() / per_k);

@@ -86,18 +86,19 @@ def test_tuning_knobs_round_trip(lib):
     before = pcc.pcc_get_tuning()
     try:
         pcc.pcc_set_tuning(stage_k=64, cluster=1, band_rows=7, cost_c0=11.0,
-                           cost_c1=3.0, pair_mma=0)
+                           cost_c1=3.0, pair_mma=0, perm_workspace=0)
         t = pcc.pcc_get_tuning()
         assert t == dict(stage_k=64, cluster=1, band_rows=7, cost_c0=11.0,
-                         cost_c1=3.0, pair_mma=0)
+                         cost_c1=3.0, pair_mma=0, perm_workspace=0)
         pcc.pcc_set_tuning()  # zeros keep every value
         assert pcc.pcc_get_tuning() == t
         for bad in (dict(stage_k=48), dict(cluster=3), dict(band_rows=-2),
-                    dict(pair_mma=2)):
+                    dict(pair_mma=2), dict(perm_workspace=-1)):
             with pytest.raises(pcc.PccError):
                 pcc.pcc_set_tuning(**bad)
         assert pcc.pcc_get_tuning() == t
     finally:
         pcc.pcc_set_tuning(before["stage_k"], before["cluster"],
                            before["band_rows"], before["cost_c0"],
-                           before["cost_c1"], before["pair_mma"])
+                           before["cost_c1"], before["pair_mma"],
+                           before["perm_workspace"])

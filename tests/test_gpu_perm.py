@@ -89,9 +89,9 @@ def test_split_ranges_accumulate(pcc_gpu):
 
 
 def test_small_workspace_batches(pcc_gpu, tmp_path):
-    """With a workspace that holds only 3 permutations the range runs as 9
-    batches; the counts equal the single-batch run (fresh process: the
-    budget is read when the library first needs it)."""
+    """The workspace form with a workspace that holds only 3 permutations
+    runs the range as 9 batches; the counts equal the single-batch run
+    (fresh process: the budget is read when the library first needs it)."""
     import os
     import subprocess
     import sys
@@ -113,20 +113,33 @@ def test_small_workspace_batches(pcc_gpu, tmp_path):
                                  str(tmp_path / "p.npy"),
                                  str(tmp_path / "g.npy")))
     per_k = 260 * 128 * 4
-    env = dict(os.environ, PCC_PERM_WS_BYTES=str(3 * per_k))
+    env = dict(os.environ, PCC_PERM_WS_BYTES=str(3 * per_k),
+               PCC_PERM_WORKSPACE="1")
     r = subprocess.run([sys.executable, "-c", code], env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     assert np.array_equal(np.load(tmp_path / "g.npy"), whole)
 
 
-def test_bad_permutation_index_is_reported(pcc_gpu):
+@pytest.mark.parametrize("workspace", [0, 1])
+def test_bad_permutation_index_is_reported(pcc_gpu, workspace):
+    """Both forms check every index: out of range is read as sample 0 and
+    recorded; the other permutations' counts are unaffected."""
     X = synth.counts_log(200, 32, seed=5)
     perms = synth.fisher_yates_perms(4, 32, seed=6)
+    good, st0, _ = gpu_perm_counts(pcc_gpu, X, perms[:2])
     perms[2, 7] = 32   # out of range
     perms[3, 0] = -1
-    _, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
-    assert st == pcc_gpu.PCC_ERR_INVALID_ARG
+    before = pcc_gpu.pcc_get_tuning()
+    try:
+        pcc_gpu.pcc_set_tuning(perm_workspace=workspace)
+        got, st, _ = gpu_perm_counts(pcc_gpu, X, perms, ranges=[(0, 2)])
+        _, st2, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    finally:
+        pcc_gpu.pcc_set_tuning(perm_workspace=before["perm_workspace"])
+    assert st0 == 0 and st == 0
+    assert np.array_equal(got, good)
+    assert st2 == pcc_gpu.PCC_ERR_INVALID_ARG
 
 
 def test_invalid_ranges(pcc_gpu):
@@ -214,3 +227,41 @@ def test_perm_counts_long_rows(pcc_gpu, l):
     I, J = np.triu_indices(n, 1)
     exact, total = check_band(X, perms, got, I, J)
     assert exact > 0.5 * total
+
+
+@pytest.mark.parametrize("n,l,P,prec", [
+    (300, 33, 41, "fp16x3s"),    # 3 tile columns: a dummy partner tile
+    (520, 200, 40, "bf16x3"),    # 5 tile columns
+    (129, 64, 7, "fp16x3s"),     # two tile columns, odd P
+    (400, 256, 17, "bf16x4"),    # the longest rows of the form, lo.lo
+    (260, 96, 1, "fp16x3s"),     # one permutation: a lone pass only
+    (700, 130, 2, "bf16x3"),     # one full pass per tile
+])
+def test_perm_smem_equals_workspace(pcc_gpu, n, l, P, prec):
+    """CTA pairs that permute the column rows in shared memory give the
+    workspace form's counts exactly (same MMAs on the same operands),
+    including a column's lone last tile, an odd number of permutations, a
+    single permutation and resumed ranges that cut the pass sequence."""
+    pcc = pcc_gpu
+    X = synth.counts_log(n, l, seed=3 * n + l)
+    X[n // 4] = 0.5  # flagged row: counts stay 0
+    perms = synth.fisher_yates_perms(P, l, seed=P + l)
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(pair_mma=1, perm_workspace=1)
+        ref, st0, Z = gpu_perm_counts(pcc, X, perms, prec)
+        pcc.pcc_set_tuning(perm_workspace=0)
+        got, st1, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z)
+        cut = [(0, P // 3), (P // 3, P)] if P > 2 else [(0, 1), (1, P)]
+        part, st2, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z,
+                                       ranges=[r for r in cut if r[1] > r[0]])
+    finally:
+        pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
+                           perm_workspace=before["perm_workspace"])
+    assert st0 == st1 == st2 == 0
+    assert ref.max() > 0
+    assert np.array_equal(got, ref)
+    assert np.array_equal(part, ref)
+    I, J = np.triu_indices(n, 1)
+    exact, tot = check_band(X, perms, got, I, J)
+    assert exact > 0.5 * tot
