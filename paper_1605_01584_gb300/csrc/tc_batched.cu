@@ -90,8 +90,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kStageBytes = C::kStageBytes;
   constexpr int kStages = C::kStages;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, kept as an offset from the shared array so
+  // that accesses through it compile to shared-memory instructions
+  uint8_t* smem =
+      smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* ring = smem;
   float* epi = reinterpret_cast<float*>(smem + kStages * kStageBytes);
   uint64_t* bars =

@@ -256,8 +256,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                               2 * kPT);
 
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // 1024-byte aligned base, kept as an offset from the shared array so
+  // that accesses through it compile to shared-memory instructions
+  uint8_t* smem =
+      smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t* aregion = smem;                 // resident A (RESA)
   uint8_t* ring = smem + C::kABytes;
   uint64_t* bars =
