@@ -39,9 +39,10 @@
 // tensor cores' 48 KB of operand reads, 16 KB of gather reads and 16 KB of
 // stores, 16 KB of A copies) against 64 KB when the permuted rows arrive by
 // TMA next to a resident A tile: about as many cycles of shared-memory
-// bandwidth as the stage's MMAs take.  This form is therefore slower than
-// the workspace form (tc_perm.cu) and serves where its workspace does not
-// fit or is not wanted.
+// bandwidth as the stage's MMAs take, so this form can at best match the
+// workspace form (tc_perm.cu).  As built it runs well below that bound,
+// stalled on each stage's per-warp waits and hand-offs, and it serves where
+// the workspace does not fit or is not wanted.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
