@@ -11,7 +11,7 @@
 //                  index: an index outside [0, l) is recorded as
 //                  PCC_ERR_INVALID_ARG and read as sample 0, never out of
 //                  bounds).
-//   k_perm_tc      a persistent kernel over work items (chunk of ~48
+//   k_perm_tc      a persistent kernel over work items (chunk of ~192
 //                  permutations, 128 x 128 tile of the triangle), chunk-major
 //                  and column by column so that concurrent CTAs reuse the
 //                  same permuted column panels from L2.  Per item: the A
@@ -45,7 +45,7 @@ namespace pcc {
 namespace {
 
 constexpr int kPThreads = 320;
-constexpr int64_t kPermChunk = 48;           // permutations per work item
+constexpr int64_t kPermChunk = 192;          // permutations per work item
 
 // column-major numbering of the upper triangle of tiles (diagonal in):
 // column x holds tiles (0..x, x), F(x) = x(x+1)/2 tiles before it; the
@@ -775,9 +775,10 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
     if (!encode_tmap_3d_u16(&ph, wh, kbatch, n, lpad, kPT, KP, bf16) ||
         !encode_tmap_3d_u16(&pl, wl, kbatch, n, lpad, kPT, KP, bf16))
       return PCC_ERR_CUDA;
-    // chunks of about kPermChunk permutations: short enough that the
-    // permuted panels in flight fit in L2, long enough that r_obs (one
-    // extra pass per item) stays a few percent; and at least ~8 items per SM
+    // chunks of about kPermChunk permutations, and at least ~8 items per
+    // worker: each item repeats the r_obs pass, which costs more than the
+    // L2 reuse of permuted panels that shorter chunks buy (4,096 x 256 x
+    // 1,000 on CTA pairs: 48 -> 8.9 ms, 96 -> 8.7, 192 -> 8.5, 336 -> 8.4)
     const int64_t workers = pair ? sms / 2 : sms;  // CTAs or CTA pairs
     int64_t chunk = kPermChunk;
     if (tiles * ((kbatch + chunk - 1) / chunk) < 8 * workers)
