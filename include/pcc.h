@@ -308,7 +308,7 @@ pcc_status pcc_edges_copy_host(const pcc_edge *edges, const uint64_t *d_count,
  *   - the shared-memory form (pcc_set_perm_workspace(0), CTA pairs, rows of
  *     up to 256 padded samples): each CTA keeps 64 of the column tile's
  *     rows z_j resident in shared memory and builds every permuted operand
- *     there; no device memory is allocated, at about 2.5 times the
+ *     there; no device memory is allocated, at about 2.6 times the
  *     workspace form's time (shared-memory bandwidth).
  * Errors: PCC_ERR_INVALID_ARG for a bad range, NULL pointers or a non
  * tensor-core Z. */
