@@ -265,3 +265,25 @@ def test_perm_smem_equals_workspace(pcc_gpu, n, l, P, prec):
     I, J = np.triu_indices(n, 1)
     exact, tot = check_band(X, perms, got, I, J)
     assert exact > 0.5 * tot
+
+
+@pytest.mark.parametrize("n,l,pair", [(300, 64, 0), (260, 300, 1)])
+def test_perm_smem_switch_falls_back(pcc_gpu, n, l, pair):
+    """Where the shared-memory form does not apply (single CTAs, or rows
+    longer than 256 samples), selecting it runs the workspace form: the
+    counts equal the workspace form's."""
+    pcc = pcc_gpu
+    X = synth.counts_log(n, l, seed=n + l)
+    perms = synth.fisher_yates_perms(9, l, seed=l)
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(pair_mma=pair, perm_workspace=1)
+        ref, st0, Z = gpu_perm_counts(pcc, X, perms, "bf16x3")
+        pcc.pcc_set_tuning(perm_workspace=0)
+        got, st1, _ = gpu_perm_counts(pcc, X, perms, "bf16x3", Z=Z)
+    finally:
+        pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
+                           perm_workspace=before["perm_workspace"])
+    assert st0 == st1 == 0
+    assert ref.max() > 0
+    assert np.array_equal(got, ref)
