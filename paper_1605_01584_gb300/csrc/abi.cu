@@ -410,6 +410,7 @@ pcc_status pcc_zmat_destroy(pcc_zmat* Z) {
   if (Z->win_ws) cudaFree(Z->win_ws);
   if (Z->stage_ws) cudaFreeHost(Z->stage_ws);
   if (Z->xin_ws) cudaFree(Z->xin_ws);
+  if (Z->zt) cudaFree(Z->zt);
   cudaError_t e = cudaFree(Z->base);
   if (cur != Z->device) cudaSetDevice(cur);
   free(Z);

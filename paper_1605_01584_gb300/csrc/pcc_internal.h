@@ -37,6 +37,11 @@ struct pcc_zmat {
   // device copy of a host input (pcc_standardize_host), kept between calls
   void* xin_ws;
   size_t xin_ws_bytes;
+  // FP32 form: the k-major copy the CUDA-core pair kernel reads (made by
+  // its first call after each standardize, which clears zt_valid)
+  void* zt;
+  size_t zt_bytes;
+  int zt_valid;
 };
 
 namespace pcc {

@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "pcc_internal.h"
+#include "pcc_ptx.cuh"
 #include "pcc_sched.h"
 
 namespace pcc {
@@ -58,6 +59,97 @@ struct SimtCross {
   int64_t r_off;           // R holds the output from element r_off on
 };
 
+// Stores of a finished tile, called by all NT threads of the block: thread
+// (tx, ty) holds rows g * BT/GR + ty * W + a and columns h * BT/2 + tx * W + b
+// of the tile in acc[g * W + a][h * W + b]; smem holds at least BT/2 rows of
+// BT + 4 values (the operand stages, free once the K loop is over).  Each
+// half of the tile's rows goes through shared memory, so that a warp writes
+// 32 consecutive pairs of one row per instruction (a packed row's pairs are
+// contiguous; the threads' register blocks would touch 16 sectors per store
+// instruction).  fr/fc: flags of the tile's rows and columns.
+template <typename T, typename OutT, int BT, int GR, int NT, bool WRITE_R,
+          bool EDGES, bool CROSS>
+__device__ __forceinline__ void store_tile(
+    const T (&acc)[GR * Vec16<T>::W][2 * Vec16<T>::W], T* smem_ops,
+    const uint8_t* fr, const uint8_t* fc, int tid, int64_t row0,
+    int64_t col0, int64_t n, int64_t nb, OutT* R, float tau,
+    pcc_edge* edges, uint64_t cap, unsigned long long* count, int* status,
+    const SimtCross& cx) {
+  using V = typename Vec16<T>::type;
+  constexpr int W = Vec16<T>::W;
+  constexpr int PAD = 4;
+  constexpr int NWARP = NT / 32;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, warp = tid >> 5;
+  T(*tile)[BT + PAD] = reinterpret_cast<T(*)[BT + PAD]>(smem_ops);
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    __syncthreads();  // operand stages (or the previous half) are free
+    // row groups g of this half: g * BT/GR in [half * BT/2, (half+1) BT/2)
+#pragma unroll
+    for (int g = half * GR / 2; g < (half + 1) * GR / 2; ++g) {
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        const int li = g * (BT / GR) - half * (BT / 2) + ty * W + a;
+        const T* q = acc[g * W + a];
+        V v0, v1;
+        if constexpr (W == 4) {
+          v0 = make_float4(q[0], q[1], q[2], q[3]);
+          v1 = make_float4(q[4], q[5], q[6], q[7]);
+        } else {
+          v0 = make_double2(q[0], q[1]);
+          v1 = make_double2(q[2], q[3]);
+        }
+        *reinterpret_cast<V*>(&tile[li][tx * W]) = v0;
+        *reinterpret_cast<V*>(&tile[li][BT / 2 + tx * W]) = v1;
+      }
+    }
+    __syncthreads();
+    for (int li = warp; li < BT / 2; li += NWARP) {
+      const int ri = half * (BT / 2) + li;  // row within the tile
+      const int64_t i = row0 + ri;
+      if (i >= n) break;
+      const int64_t base =
+          (CROSS ? i * cx.ldr : pair_row_base(n, i)) - cx.r_off;
+#pragma unroll
+      for (int c = 0; c < BT / 32; ++c) {
+        const int lj = c * 32 + lane;
+        const int64_t j = col0 + lj;
+        const bool valid = (j < nb) && (CROSS || j > i);
+        const bool flagged = (fr[ri] | fc[lj]) != 0;
+        T v = tile[li][lj];
+        v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
+        if (flagged) v = T(NAN);
+        if constexpr (WRITE_R) {
+          if (valid) R[base + j] = (OutT)v;
+        }
+        if constexpr (EDGES) {
+          const bool e = valid && !flagged && fabs((double)v) >= (double)tau;
+          const unsigned mask = __ballot_sync(0xffffffffu, e);
+          if (mask) {
+            const int leader = __ffs(mask) - 1;
+            unsigned long long basei = 0;
+            if (lane == leader)
+              basei = atomicAdd(count, (unsigned long long)__popc(mask));
+            basei = __shfl_sync(0xffffffffu, basei, leader);
+            if (e) {
+              const unsigned long long idx =
+                  basei + __popc(mask & ((1u << lane) - 1u));
+              if (idx < cap) {
+                edges[idx].i = (uint32_t)i;
+                edges[idx].j = (uint32_t)j;
+                edges[idx].r = (float)v;
+              } else {
+                atomicCAS(status, 0, (int)PCC_ERR_CAPACITY);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // Thread layout: NT threads as 16 columns (tx) x NT/16 rows (ty) of
 // threads; with W = 16 bytes / sizeof(T) (one vector), thread (tx, ty) owns
 // the W x W blocks at rows g * BT/GR + ty * W (g < GR groups) and columns
@@ -84,7 +176,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 3)
   static_assert(NTY * W * GR == BT && 16 * W * 2 == BT, "thread layout");
   constexpr int PAD = 4;
   constexpr int NV = BT * BK / NT / W;  // vector loads per thread/operand
-  constexpr int NWARP = NT / 32;
 
   // operand stages; after the K loop the same memory stages the tile for
   // the stores, half of its rows at a time
@@ -190,78 +281,208 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 3)
     }
   }
 
-  // Stores: each half of the tile's rows goes through shared memory, so
-  // that a warp writes 32 consecutive pairs of one row per instruction (a
-  // packed row's pairs are contiguous; the threads' register blocks would
-  // touch 16 sectors per store instruction).
-  const int lane = tid & 31, warp = tid >> 5;
-  T(*tile)[BT + PAD] = reinterpret_cast<T(*)[BT + PAD]>(smem_ops);
+  store_tile<T, OutT, BT, GR, NT, WRITE_R, EDGES, CROSS>(
+      acc, smem_ops, fr, fc, tid, row0, col0, n, nb, R, tau, edges, cap,
+      count, status, cx);
+}
+
+// ---------------------------------------------------------------- FP32, k-major
+// FP32 pairs from k-major copies of Z (ZT: lpad rows of npad values, value
+// (k, i) = z_i[k], npad = n rounded up to the tile with zeros beyond n).
+// The BK x BT slice of a tile's rows at one K block is then BK contiguous
+// runs of BT values, which 16-byte cp.async copies move to shared memory as
+// they are, in a ring of kKmS stages: no staging through registers and no
+// transposing stores, so the loop issues little besides the 64 FMAs per k
+// of a thread's 8 x 8 block (same thread layout and store path as above).
+constexpr int kKmBT = 128, kKmNT = 256, kKmBK = 16, kKmS = 4;
+constexpr int kKmStage = 2 * kKmBK * kKmBT;         // floats: A, then B
+constexpr int kKmSmemBytes = kKmS * kKmStage * 4;   // 64 KB
+static_assert(kKmBT / 2 * (kKmBT + 4) <= kKmS * kKmStage,
+              "the tile's staging for the stores fits the ring");
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+               "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <bool WRITE_R, bool EDGES, bool CROSS>
+__global__ void __launch_bounds__(kKmNT, 2)
+    k_pairs_simt_km(const float* __restrict__ ZT,
+                    const float* __restrict__ ZTb,
+                    const uint8_t* __restrict__ flags, int64_t n,
+                    int64_t npad, int64_t npadb, int64_t lpad, int64_t m,
+                    int64_t t0, float* __restrict__ R, float tau,
+                    pcc_edge* __restrict__ edges, uint64_t cap,
+                    unsigned long long* __restrict__ count,
+                    int* __restrict__ status, const SimtCross cx) {
+  constexpr int BT = kKmBT, BK = kKmBK, S = kKmS, NT = kKmNT;
+  const uint8_t* __restrict__ flagsb = CROSS ? cx.flagsb : flags;
+  const int64_t nb = CROSS ? cx.nb : n;
+  extern __shared__ __align__(16) float km_smem[];
+  __shared__ uint8_t fr[BT], fc[BT];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  int64_t yt, xt;
+  if constexpr (CROSS) {
+    const int64_t t = t0 + (int64_t)blockIdx.x;
+    yt = t / cx.mb;  // Eq. (8)
+    xt = t - yt * cx.mb;
+  } else {
+    tri_coords(m, t0 + (int64_t)blockIdx.x, &yt, &xt);
+  }
+  const int64_t row0 = yt * BT, col0 = xt * BT;
+  for (int t = tid; t < BT; t += NT) {
+    fr[t] = (row0 + t < n) ? flags[row0 + t] : 1;
+    fc[t] = (col0 + t < nb) ? flagsb[col0 + t] : 1;
+  }
+
+  // stage s: A rows [BK][BT] at s * kKmStage, B rows right after; a thread
+  // copies chunks tid + NT * i (i < 4) of the stage's 1,024 16-byte chunks,
+  // so each warp copies 512 contiguous bytes of one k row
+  const uint32_t sbase = smem_u32(km_smem);
+  auto load_stage = [&](int s, int64_t kb) {
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    __syncthreads();  // operand stages (or the previous half) are free
-    // row groups g of this half: g * BT/GR in [half * BT/2, (half+1) BT/2)
-#pragma unroll
-    for (int g = half * GR / 2; g < (half + 1) * GR / 2; ++g) {
-#pragma unroll
-      for (int a = 0; a < W; ++a) {
-        const int li = g * (BT / GR) - half * (BT / 2) + ty * W + a;
-        const T* q = acc[g * W + a];
-        V v0, v1;
-        if constexpr (W == 4) {
-          v0 = make_float4(q[0], q[1], q[2], q[3]);
-          v1 = make_float4(q[4], q[5], q[6], q[7]);
-        } else {
-          v0 = make_double2(q[0], q[1]);
-          v1 = make_double2(q[2], q[3]);
-        }
-        *reinterpret_cast<V*>(&tile[li][tx * W]) = v0;
-        *reinterpret_cast<V*>(&tile[li][BT / 2 + tx * W]) = v1;
-      }
+    for (int i = 0; i < 4; ++i) {
+      const int c = tid + i * NT;
+      const int op = c >> 9;  // 0: A (rows of the tile), 1: B (columns)
+      const int kr = (c & 511) >> 5, c4 = c & 31;
+      const int64_t k = kb * BK + kr;
+      const float* src = op ? ZTb + k * npadb + col0 + c4 * 4
+                            : ZT + k * npad + row0 + c4 * 4;
+      cp_async16(sbase + (uint32_t)((s * kKmStage + op * BK * BT + kr * BT +
+                                     c4 * 4) * 4),
+                 src);
     }
-    __syncthreads();
-    for (int li = warp; li < BT / 2; li += NWARP) {
-      const int ri = half * (BT / 2) + li;  // row within the tile
-      const int64_t i = row0 + ri;
-      if (i >= n) break;
-      const int64_t base =
-          (CROSS ? i * cx.ldr : pair_row_base(n, i)) - cx.r_off;
+  };
+
+  float acc[8][8];
 #pragma unroll
-      for (int c = 0; c < BT / 32; ++c) {
-        const int lj = c * 32 + lane;
-        const int64_t j = col0 + lj;
-        const bool valid = (j < nb) && (CROSS || j > i);
-        const bool flagged = (fr[ri] | fc[lj]) != 0;
-        T v = tile[li][lj];
-        v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
-        if (flagged) v = T(NAN);
-        if constexpr (WRITE_R) {
-          if (valid) R[base + j] = (OutT)v;
-        }
-        if constexpr (EDGES) {
-          const bool e = valid && !flagged && fabs((double)v) >= (double)tau;
-          const unsigned mask = __ballot_sync(0xffffffffu, e);
-          if (mask) {
-            const int leader = __ffs(mask) - 1;
-            unsigned long long basei = 0;
-            if (lane == leader)
-              basei = atomicAdd(count, (unsigned long long)__popc(mask));
-            basei = __shfl_sync(0xffffffffu, basei, leader);
-            if (e) {
-              const unsigned long long idx =
-                  basei + __popc(mask & ((1u << lane) - 1u));
-              if (idx < cap) {
-                edges[idx].i = (uint32_t)i;
-                edges[idx].j = (uint32_t)j;
-                edges[idx].r = (float)v;
-              } else {
-                atomicCAS(status, 0, (int)PCC_ERR_CAPACITY);
-              }
-            }
-          }
-        }
-      }
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+  const int64_t nkb = lpad / BK;
+#pragma unroll
+  for (int s = 0; s < S - 1; ++s) {
+    if (s < nkb) load_stage(s, s);
+    cp_async_commit();
+  }
+  for (int64_t kb = 0; kb < nkb; ++kb) {
+    // stage kb has landed, and every thread is done with stage kb - 1,
+    // whose buffer the next copy reuses
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    const int64_t kn = kb + S - 1;
+    if (kn < nkb) load_stage((int)(kn % S), kn);
+    cp_async_commit();
+    const float* As = km_smem + (int)(kb % S) * kKmStage;
+    const float* Bs = As + BK * BT;
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(As + k * BT + ty * 4);
+      const float4 a1 =
+          *reinterpret_cast<const float4*>(As + k * BT + BT / 2 + ty * 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(Bs + k * BT + tx * 4);
+      const float4 b1 =
+          *reinterpret_cast<const float4*>(Bs + k * BT + BT / 2 + tx * 4);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
   }
+  cp_async_wait<0>();
+  store_tile<float, float, BT, 2, NT, WRITE_R, EDGES, CROSS>(
+      acc, km_smem, fr, fc, tid, row0, col0, n, nb, R, tau, edges, cap,
+      count, status, cx);
+}
+
+// ZT[k][i] = Z[i][k] for k < lpad, i < npad (zero for i >= n), through a
+// 32 x 33 shared tile so that both the reads and the writes are coalesced.
+__global__ void __launch_bounds__(256)
+    k_transpose_f32(const float* __restrict__ Z, int64_t n, int64_t lpad,
+                    float* __restrict__ ZT, int64_t npad) {
+  __shared__ float t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int64_t i = i0 + r;
+    t[r][threadIdx.x] = i < n ? Z[i * lpad + k0 + threadIdx.x] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8)
+    ZT[(k0 + r) * npad + i0 + threadIdx.x] = t[threadIdx.x][r];
+}
+
+int64_t km_npad(int64_t n) { return (n + kKmBT - 1) / kKmBT * kKmBT; }
+
+// The k-major copy of an FP32 Z, made once after each standardize (the
+// standardize entry points clear zt_valid); kept in Z.
+cudaError_t ensure_zt(const pcc_zmat* Zc, cudaStream_t s) {
+  pcc_zmat* Z = const_cast<pcc_zmat*>(Zc);
+  if (Z->zt_valid) return cudaSuccess;
+  const int64_t npad = km_npad(Z->n);
+  const size_t need = (size_t)npad * (size_t)Z->lpad * sizeof(float);
+  if (Z->zt_bytes < need) {
+    if (Z->zt) {
+      cudaStreamSynchronize(s);
+      cudaFree(Z->zt);
+      Z->zt = nullptr;
+      Z->zt_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&Z->zt, need);
+    if (e != cudaSuccess) return e;
+    Z->zt_bytes = need;
+  }
+  k_transpose_f32<<<dim3((unsigned)(npad / 32), (unsigned)(Z->lpad / 32)),
+                    dim3(32, 8), 0, s>>>(static_cast<const float*>(Z->z),
+                                         Z->n, Z->lpad,
+                                         static_cast<float*>(Z->zt), npad);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) Z->zt_valid = 1;
+  return e;
+}
+
+template <bool CROSS>
+cudaError_t launch_km(const pcc_zmat* Z, const pcc_zmat* ZB, float* R,
+                      int64_t t0, int64_t t1, bool edges_on, float tau,
+                      pcc_edge* edges, uint64_t cap,
+                      unsigned long long* count, cudaStream_t s,
+                      const SimtCross& cx) {
+  const int64_t m = (Z->n + kKmBT - 1) / kKmBT;
+  const int64_t nblocks = t1 - t0;
+  if (nblocks <= 0) return cudaSuccess;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  cudaError_t e = ensure_zt(Z, s);
+  if (e == cudaSuccess && CROSS) e = ensure_zt(ZB, s);
+  if (e != cudaSuccess) return e;
+  const float* zt = static_cast<const float*>(Z->zt);
+  const float* ztb = static_cast<const float*>(CROSS ? ZB->zt : Z->zt);
+  const int64_t npad = km_npad(Z->n), npadb = km_npad(ZB->n);
+  auto go = [&](auto fn) {
+    cudaError_t r = ensure_func_smem(reinterpret_cast<const void*>(fn),
+                                     kKmSmemBytes);
+    if (r != cudaSuccess) return r;
+    fn<<<(unsigned)nblocks, kKmNT, kKmSmemBytes, s>>>(
+        zt, ztb, Z->flags, Z->n, npad, npadb, Z->lpad, m, t0, R, tau, edges,
+        cap, count, Z->status, cx);
+    return cudaGetLastError();
+  };
+  if (edges_on && R) return go(k_pairs_simt_km<true, true, CROSS>);
+  if (edges_on) return go(k_pairs_simt_km<false, true, CROSS>);
+  return go(k_pairs_simt_km<true, false, CROSS>);
 }
 
 template <typename T, typename OutT, int BT, int GR, int NT, bool CROSS>
@@ -293,15 +514,15 @@ cudaError_t launch_t(const pcc_zmat* Z, OutT* R, int64_t t0, int64_t t1,
 }
 
 template <bool CROSS>
-cudaError_t launch_prec(const pcc_zmat* Z, void* R, pcc_dtype rt, int64_t t0,
-                        int64_t t1, float tau, pcc_edge* edges, uint64_t cap,
+cudaError_t launch_prec(const pcc_zmat* Z, const pcc_zmat* ZB, void* R,
+                        pcc_dtype rt, int64_t t0, int64_t t1, float tau,
+                        pcc_edge* edges, uint64_t cap,
                         unsigned long long* count, cudaStream_t s,
                         const SimtCross& cx) {
   const bool edges_on = count != nullptr;
   if (Z->prec == PCC_PREC_FP32)
-    return launch_t<float, float, 128, 2, 256, CROSS>(
-        Z, reinterpret_cast<float*>(R), t0, t1, edges_on, tau, edges, cap,
-        count, s, cx);
+    return launch_km<CROSS>(Z, ZB, reinterpret_cast<float*>(R), t0, t1,
+                            edges_on, tau, edges, cap, count, s, cx);
   if (rt == PCC_F64)
     return launch_t<double, double, 64, 2, 256, CROSS>(
         Z, reinterpret_cast<double*>(R), t0, t1, edges_on, tau, edges, cap,
@@ -321,7 +542,8 @@ cudaError_t launch_simt_pairs(const pcc_zmat* Z, void* R, pcc_dtype rt,
                               unsigned long long* count, cudaStream_t s,
                               int64_t r_off) {
   const SimtCross cx{Z->z, Z->flags, Z->n, 0, 0, r_off};
-  return launch_prec<false>(Z, R, rt, t0, t1, tau, edges, cap, count, s, cx);
+  return launch_prec<false>(Z, Z, R, rt, t0, t1, tau, edges, cap, count, s,
+                            cx);
 }
 
 int64_t simt_cross_tiles(const pcc_zmat* ZA, const pcc_zmat* ZB) {
@@ -337,7 +559,8 @@ cudaError_t launch_simt_cross(const pcc_zmat* ZA, const pcc_zmat* ZB, void* R,
   const int64_t t = simt_tile_size(ZA->prec);
   const SimtCross cx{ZB->z, ZB->flags, ZB->n, (ZB->n + t - 1) / t, ldr,
                      r_off};
-  return launch_prec<true>(ZA, R, rt, t0, t1, tau, edges, cap, count, s, cx);
+  return launch_prec<true>(ZA, ZB, R, rt, t0, t1, tau, edges, cap, count, s,
+                           cx);
 }
 
 }  // namespace pcc

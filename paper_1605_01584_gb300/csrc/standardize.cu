@@ -407,6 +407,7 @@ cudaError_t launch_mode(const TX* X, int64_t ldx, pcc_zmat* Z,
 
 cudaError_t launch_standardize(const void* X, pcc_dtype xt, int64_t ldx,
                                pcc_zmat* Z, cudaStream_t s) {
+  Z->zt_valid = 0;  // the FP32 form's k-major copy is out of date
   if (xt == PCC_F64)
     return launch_mode(reinterpret_cast<const double*>(X), ldx, Z, s);
   return launch_mode(reinterpret_cast<const float*>(X), ldx, Z, s);
@@ -418,6 +419,7 @@ cudaError_t launch_standardize_batched(const float* const* Xs,
   // one launch per stored form; the FP64 form has no FP32 row loop here
   const pcc_prec forms[4] = {PCC_PREC_BF16X3, PCC_PREC_FP16X3S,
                              PCC_PREC_BF16X1, PCC_PREC_FP32};
+  for (int b = 0; b < count; ++b) Zs[b]->zt_valid = 0;
   for (int f = 0; f < 4; ++f) {
     int b = 0;
     while (b < count) {
