@@ -124,7 +124,14 @@ __device__ __forceinline__ void store_tile(
           if (valid) R[base + j] = (OutT)v;
         }
         if constexpr (EDGES) {
-          const bool e = valid && !flagged && fabs((double)v) >= (double)tau;
+          // FP32 values compare in FP32: the same result as in FP64 (both
+          // conversions are exact) without the slow FP64 pipe
+          bool over;
+          if constexpr (sizeof(T) == 4)
+            over = fabsf((float)v) >= tau;
+          else
+            over = fabs((double)v) >= (double)tau;
+          const bool e = valid && !flagged && over;
           const unsigned mask = __ballot_sync(0xffffffffu, e);
           if (mask) {
             const int leader = __ffs(mask) - 1;
