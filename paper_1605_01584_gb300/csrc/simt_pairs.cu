@@ -41,10 +41,6 @@ struct Vec16<double> {
 template <typename V, typename T>
 __device__ __forceinline__ T vget(const V& v, int q);
 template <>
-__device__ __forceinline__ float vget<float4, float>(const float4& v, int q) {
-  return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-template <>
 __device__ __forceinline__ double vget<double2, double>(const double2& v,
                                                        int q) {
   return q == 0 ? v.x : v.y;
@@ -80,7 +76,15 @@ __device__ __forceinline__ void store_tile(
   constexpr int PAD = 4;
   constexpr int NWARP = NT / 32;
   const int tx = tid & 15, ty = tid >> 4;
-  const int lane = tid & 31, warp = tid >> 5;
+  const int lane = tid & 31;
+  // this lane's columns of the tile: flags and bounds, fixed for the tile
+  bool cfl[BT / 32], cin[BT / 32];
+#pragma unroll
+  for (int c = 0; c < BT / 32; ++c) {
+    cfl[c] = fc[c * 32 + lane] != 0;
+    cin[c] = col0 + c * 32 + lane < nb;
+  }
+  const int warp = tid >> 5;
   T(*tile)[BT + PAD] = reinterpret_cast<T(*)[BT + PAD]>(smem_ops);
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
@@ -111,12 +115,13 @@ __device__ __forceinline__ void store_tile(
       if (i >= n) break;
       const int64_t base =
           (CROSS ? i * cx.ldr : pair_row_base(n, i)) - cx.r_off;
+      const bool rfl = fr[ri] != 0;
 #pragma unroll
       for (int c = 0; c < BT / 32; ++c) {
         const int lj = c * 32 + lane;
         const int64_t j = col0 + lj;
-        const bool valid = (j < nb) && (CROSS || j > i);
-        const bool flagged = (fr[ri] | fc[lj]) != 0;
+        const bool valid = cin[c] && (CROSS || j > i);
+        const bool flagged = rfl || cfl[c];
         T v = tile[li][lj];
         v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
         if (flagged) v = T(NAN);
@@ -161,10 +166,9 @@ __device__ __forceinline__ void store_tile(
 // threads; with W = 16 bytes / sizeof(T) (one vector), thread (tx, ty) owns
 // the W x W blocks at rows g * BT/GR + ty * W (g < GR groups) and columns
 // h * BT/2 + tx * W (h < 2): TR = GR * W rows by TC = 2 * W columns, read per
-// k as GR + 2 vectors of shared memory.  FP32 runs 256 threads of 8 x 8,
-// FP64 256 threads of 4 x 4.  (128 FP32 threads of 16 x 8, 6 vector loads
-// per 128 FMAs instead of 4 per 64, took 50.8 ms at 65,536 x 512 against
-// 46.6: two blocks of 4 warps per SM hide less than two of 8.)
+// k as GR + 2 vectors of shared memory.  This row-major form serves FP64
+// (256 threads of 4 x 4); FP32 uses the k-major form below with the same
+// thread layout (256 threads of 8 x 8).
 template <typename T, typename OutT, int BT, int GR, int NT, int BK,
           bool WRITE_R, bool EDGES, bool CROSS>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 3)
