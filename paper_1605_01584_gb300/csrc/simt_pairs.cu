@@ -109,6 +109,29 @@ __device__ __forceinline__ void store_tile(
       }
     }
     __syncthreads();
+    // the value stored for row li, column chunk c of this half (clamped,
+    // NaN when flagged), whether it is a pair of the output, and whether
+    // it is an edge
+    auto value = [&](int li, int c, int64_t i, bool rfl, bool* valid,
+                     bool* edge) -> T {
+      const int lj = c * 32 + lane;
+      const int64_t j = col0 + lj;
+      *valid = cin[c] && (CROSS || j > i);
+      const bool flagged = rfl || cfl[c];
+      T v = tile[li][lj];
+      v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
+      if (flagged) v = T(NAN);
+      // FP32 values compare in FP32: the same result as in FP64 (both
+      // conversions are exact) without the slow FP64 pipe
+      bool over;
+      if constexpr (sizeof(T) == 4)
+        over = fabsf((float)v) >= tau;
+      else
+        over = fabs((double)v) >= (double)tau;
+      *edge = *valid && !flagged && over;
+      return v;
+    };
+    bool hit = false;  // EDGES: some pair of this warp's rows is an edge
     for (int li = warp; li < BT / 2; li += NWARP) {
       const int ri = half * (BT / 2) + li;  // row within the tile
       const int64_t i = row0 + ri;
@@ -118,27 +141,28 @@ __device__ __forceinline__ void store_tile(
       const bool rfl = fr[ri] != 0;
 #pragma unroll
       for (int c = 0; c < BT / 32; ++c) {
-        const int lj = c * 32 + lane;
-        const int64_t j = col0 + lj;
-        const bool valid = cin[c] && (CROSS || j > i);
-        const bool flagged = rfl || cfl[c];
-        T v = tile[li][lj];
-        v = v > T(1) ? T(1) : (v < T(-1) ? T(-1) : v);
-        if (flagged) v = T(NAN);
+        bool valid, e;
+        const T v = value(li, c, i, rfl, &valid, &e);
         if constexpr (WRITE_R) {
-          if (valid) R[base + j] = (OutT)v;
+          if (valid) R[base + col0 + c * 32 + lane] = (OutT)v;
         }
-        if constexpr (EDGES) {
-          // FP32 values compare in FP32: the same result as in FP64 (both
-          // conversions are exact) without the slow FP64 pipe
-          bool over;
-          if constexpr (sizeof(T) == 4)
-            over = fabsf((float)v) >= tau;
-          else
-            over = fabs((double)v) >= (double)tau;
-          const bool e = valid && !flagged && over;
-          const unsigned mask = __ballot_sync(0xffffffffu, e);
-          if (mask) {
+        if constexpr (EDGES) hit |= e;
+      }
+    }
+    // edges are rare: only a warp with one rescans its rows of the staged
+    // half and appends them, one atomic per warp and 32 columns
+    if constexpr (EDGES) {
+      if (__any_sync(0xffffffffu, hit)) {
+        for (int li = warp; li < BT / 2; li += NWARP) {
+          const int ri = half * (BT / 2) + li;
+          const int64_t i = row0 + ri;
+          if (i >= n) break;
+          const bool rfl = fr[ri] != 0;
+          for (int c = 0; c < BT / 32; ++c) {
+            bool valid, e;
+            const T v = value(li, c, i, rfl, &valid, &e);
+            const unsigned mask = __ballot_sync(0xffffffffu, e);
+            if (!mask) continue;
             const int leader = __ffs(mask) - 1;
             unsigned long long basei = 0;
             if (lane == leader)
@@ -149,7 +173,7 @@ __device__ __forceinline__ void store_tile(
                   basei + __popc(mask & ((1u << lane) - 1u));
               if (idx < cap) {
                 edges[idx].i = (uint32_t)i;
-                edges[idx].j = (uint32_t)j;
+                edges[idx].j = (uint32_t)(col0 + c * 32 + lane);
                 edges[idx].r = (float)v;
               } else {
                 atomicCAS(status, 0, (int)PCC_ERR_CAPACITY);
