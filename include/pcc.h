@@ -457,10 +457,11 @@ pcc_status pcc_measure_fp32_fma(double *tflops, void *stream);
  * status word and the kernel returns early instead of hanging. */
 pcc_status pcc_set_wait_limit_ns(uint64_t ns);
 
-/* Test hook for the failure path (the paper has no counterpart).
- *   enable = 1  the TMA producer of the tensor-core pair kernel issues no
- *               loads, so every CTA's first operand wait runs out after the
- *               wait limit;
+/* Test hook for the failure path (the paper has no counterpart).  It acts
+ * on the tensor-core pair kernel and on the shared-memory form of
+ * pcc_perm_test (whose producer loads the A rows).
+ *   enable = 1  the TMA producer issues no loads, so every CTA's first
+ *               operand wait runs out after the wait limit;
  *   enable = 2  in the CTA-pair form only the odd CTA of each pair issues
  *               none (the even CTA's copies land, its MMA waits for the
  *               odd CTA's share and runs out);

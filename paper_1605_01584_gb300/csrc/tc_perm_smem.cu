@@ -89,6 +89,9 @@ struct PermSmemParams {
   uint32_t* counts;
   int* status;
   uint64_t wait_ns;
+  int drop_loads;     // test hook (pcc_debug_drop_loads): 1 = no CTA loads
+                      // A, 2 = the odd CTA of a pair loads none, 3 = the
+                      // even CTA loads none (so the waits run out)
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -259,7 +262,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
       constexpr uint32_t kABytes = 2u * kSTile;  // per CTA and stage
       int stage = 0;
       uint32_t phase = 0;
-      bool ok = true;
+      bool ok = !(p.drop_loads == 1 || (p.drop_loads == 2 && crank == 1) ||
+                  (p.drop_loads == 3 && crank == 0));
       for (int64_t u = u_begin; u < u_end && ok;) {
         const Segment g = next_segment(u, u_end, p.npass);
         u += g.q1 - g.q0;
@@ -579,7 +583,10 @@ __global__ void __launch_bounds__(kSThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // every A copy issued by either CTA has landed before a CTA may exit
+  // every A copy issued by either CTA has landed before a CTA may exit.
+  // After a wait ran out, a stage's phase may also lack gathering warps'
+  // arrivals; the drain then ends on its own time limit, well after the
+  // copies (issued before the first wait ran out) have landed.
   drain_ring<true>(full, nullptr, flog, kSStages, w, crank);
   if (warp == 1) {
     __syncwarp();
@@ -654,6 +661,7 @@ pcc_status perm_test_smem(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
   p.counts = d_counts;
   p.status = Z->status;
   p.wait_ns = wait_limit_ns();
+  p.drop_loads = debug_drop_loads();
   if (p.P <= 0) return PCC_OK;
   const bool bf16 = Z->prec != PCC_PREC_FP16X3S;
   const cudaError_t e = bf16 ? launch_smem<true>(Z, p, s)

@@ -62,3 +62,44 @@ def test_allocation_failure_is_reported(pcc_gpu):
     assert e.value.status == pcc.PCC_ERR_OOM
     Z = pcc.pcc_standardize(X + torch.arange(4.0, device="cuda"), "bf16x3")
     assert pcc.pcc_sync_status(Z) == 0
+
+
+@pytest.mark.parametrize("drop", [1, 2, 3])
+def test_perm_smem_wait_timeout_is_reported(pcc_gpu, drop):
+    """The shared-memory permutation form under the same hook: its A
+    producer issues no loads (1), or only the even (2) / odd (3) CTA of
+    each pair does; the waits run out, PCC_ERR_TIMEOUT is reported, and
+    the next test gives the workspace form's counts."""
+    import torch
+    pcc = pcc_gpu
+    n, l, P = 300, 64, 9
+    X = torch.from_numpy(synth.counts_log(n, l, 41)).cuda()
+    perms = torch.from_numpy(synth.fisher_yates_perms(P, l, seed=42)).cuda()
+    Z = pcc.pcc_standardize(X, "fp16x3s")
+    cnt = torch.zeros(n * (n - 1) // 2, dtype=torch.int32, device="cuda")
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(pair_mma=1, perm_workspace=0)
+        pcc.pcc_set_wait_limit_ns(200_000_000)  # 0.2 s
+        pcc.pcc_debug_drop_loads(drop)
+        pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
+        assert pcc.pcc_sync_status(Z) == pcc.PCC_ERR_TIMEOUT
+        pcc.pcc_debug_drop_loads(False)
+        pcc.pcc_set_wait_limit_ns(4_000_000_000)
+        assert pcc.pcc_sync_status(Z) == 0
+        cnt.zero_()
+        pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
+        assert pcc.pcc_sync_status(Z) == 0
+        got = cnt.cpu().numpy()
+        pcc.pcc_set_tuning(perm_workspace=1)
+        cnt.zero_()
+        pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
+        assert pcc.pcc_sync_status(Z) == 0
+    finally:
+        pcc.pcc_debug_drop_loads(False)
+        pcc.pcc_set_wait_limit_ns(4_000_000_000)
+        pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
+                           perm_workspace=before["perm_workspace"])
+    ref = cnt.cpu().numpy()
+    assert ref.max() > 0
+    assert np.array_equal(got, ref)
