@@ -618,14 +618,21 @@ def run_perm(args):
     ms_graph = _graph_timed(step, max(3, min(args.steps, 20)), 1)
     ms = ms_graph if ms_graph is not None else ms_stream
     st = pcc.pcc_sync_status(Z)
-    # the shared-memory form (no workspace): its time, and the same counts
+    # the forms without a workspace (0: permuted in shared memory, 2: copied
+    # from a transposed Z): their times, and the same counts
     ref_cnt = cnt.clone()
     before = pcc.pcc_get_tuning()
+    other = {}
     try:
-        pcc.pcc_set_tuning(perm_workspace=0)
-        ms_smem = _timed(step, 3, 1, stream)
-        smem_equal = bool(torch.equal(cnt, ref_cnt))
-        st_smem = pcc.pcc_sync_status(Z)
+        for form, name in ((0, "shared_memory_form"),
+                           (2, "transposed_copy_form")):
+            pcc.pcc_set_tuning(perm_workspace=form)
+            ms_f = _timed(step, 3, 1, stream)
+            other[name] = {
+                "ms_per_step": ms_f,
+                "counts_equal": bool(torch.equal(cnt, ref_cnt)),
+                "status": pcc.pcc_sync_status(Z),
+                "value": n * (n - 1) / 2 * l * P / (ms_f / 1e3) / 1e9}
     finally:
         pcc.pcc_set_tuning(perm_workspace=before["perm_workspace"])
     info = Z.info()
@@ -657,12 +664,9 @@ def run_perm(args):
                        "repeats r_obs per chunk of permutations and pads "
                        "lone tiles in the pair form (about 5% more tensor "
                        "work, not counted)"},
-           # the form that allocates nothing (pcc_set_perm_workspace(0)),
-           # stream-launched, 3 steps
-           "shared_memory_form": {
-               "ms_per_step": ms_smem, "counts_equal": smem_equal,
-               "status": st_smem,
-               "value": n * (n - 1) / 2 * l * P / (ms_smem / 1e3) / 1e9}}
+           # the forms without the permuted workspace
+           # (pcc_set_perm_workspace(0) / (2)), stream-launched, 3 steps
+           **other}
     print(json.dumps(out), flush=True)
     return 0
 

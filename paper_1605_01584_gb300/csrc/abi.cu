@@ -117,7 +117,8 @@ TcTuning g_tune = [] {
   // the workspace form of the permutation test is the faster one; the
   // shared-memory form is chosen with PCC_PERM_WORKSPACE=0
   e = getenv("PCC_PERM_WORKSPACE");
-  t.perm_workspace = (e && atoi(e) == 0) ? 0 : 1;
+  const int pw = e ? atoi(e) : 1;
+  t.perm_workspace = (pw == 0 || pw == 2) ? pw : 1;
   e = getenv("PCC_TC_ONEACC");
   const int oa = e ? atoi(e) : 0;
   t.one_acc_l = oa >= 64 ? oa : 1024;
@@ -676,7 +677,7 @@ pcc_status pcc_set_pair_mma(int32_t on) {
 int32_t pcc_get_pair_mma(void) { return tc_tuning().pair_mma; }
 
 pcc_status pcc_set_perm_workspace(int32_t on) {
-  if (on != 0 && on != 1) return PCC_ERR_INVALID_ARG;
+  if (on < 0 || on > 2) return PCC_ERR_INVALID_ARG;
   TcTuning t = tc_tuning();
   t.perm_workspace = on;
   tc_set_tuning(t);

@@ -92,7 +92,8 @@ struct TcTuning {
   int perm_workspace;  // 1 (default): the permutation test gathers
                        // permuted rows into a workspace; 0: CTA pairs
                        // permute in shared memory where rows fit
-                       // (lpad <= 256)
+                       // (lpad <= 256); 2: CTA pairs copy permuted
+                       // operands from a transposed Z (lpad <= 256)
 };
 TcTuning tc_tuning();
 void tc_set_tuning(const TcTuning& t);
@@ -177,5 +178,11 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
 bool perm_smem_applies(const pcc_zmat* Z);
 pcc_status perm_test_smem(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
                           int32_t k1, uint32_t* d_counts, cudaStream_t s);
+// K6 on CTA pairs that copy the permuted column operand from a transposed
+// copy of Z (tc_perm_mn.cu): rows of up to 256 padded samples, pair form on,
+// perm_workspace 2.
+bool perm_mn_applies(const pcc_zmat* Z);
+pcc_status perm_test_mn(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
+                        int32_t k1, uint32_t* d_counts, cudaStream_t s);
 
 }  // namespace pcc

@@ -725,6 +725,8 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
   // CTA pairs permute in shared memory where the rows fit: no workspace
   if (perm_smem_applies(Z))
     return perm_test_smem(Z, d_perms, k0, k1, d_counts, s);
+  // or copy the permuted operand from a transposed Z
+  if (perm_mn_applies(Z)) return perm_test_mn(Z, d_perms, k0, k1, d_counts, s);
   const int64_t n = Z->n, lpad = Z->lpad;
   const size_t per_k = (size_t)n * (size_t)lpad * 2 * 2;  // hi + lo
   int64_t kbmax = (int64_t)(perm_ws_budget() / per_k);

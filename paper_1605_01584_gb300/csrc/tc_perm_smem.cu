@@ -67,9 +67,6 @@ constexpr int kSBarBytes = 512;
 constexpr int kSSmemBytes =
     1024 + kSStages * kSStageBytes + kSSrcBytes + kSBarBytes;
 static_assert(kSSmemBytes <= kPSmemBudget, "shared memory");
-// counts are 16-bit per pair in registers: a segment holds at most this many
-// passes (two permutations each)
-constexpr int64_t kSMaxSegPasses = 32767;
 
 struct PermSmemParams {
   int64_t n;
@@ -93,84 +90,6 @@ struct PermSmemParams {
                       // A, 2 = the odd CTA of a pair loads none, 3 = the
                       // even CTA loads none (so the waits run out)
 };
-
-// ------------------------------------------------------------ PTX helpers
-// (stages partly written by threads instead of TMA)
-
-// Make this thread's shared-memory stores visible to the tensor cores
-// (async proxy) before it signals that the stage is full.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Release over this CTA's shared memory only, at cluster scope: with the
-// relaxed arrive after it, the gathered stage is visible to whoever
-// acquires the barrier's phase, without waiting for this thread's global
-// loads in flight (the next pass's indices), as a full release would.
-__device__ __forceinline__ void fence_release_smem_cluster() {
-  asm volatile("fence.release.sync_restrict::shared::cta.cluster;" :::
-                   "memory");
-}
-
-// Arrive on an mbarrier of either CTA of the pair (shared::cluster
-// address), relaxed: the ordering comes from the fence before it.
-__device__ __forceinline__ void mbar_arrive_relaxed_cluster(uint32_t addr) {
-  asm volatile(
-      "mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(
-          addr)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait_acq_cluster(uint64_t* bar,
-                                                          uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], "
-      "%2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// mbar_wait with acquire at cluster scope (the phase was completed by
-// threads of both CTAs); bounded like mbar_wait.
-static __device__ __noinline__ bool mbar_wait_acq_cluster(uint64_t* bar,
-                                                          uint32_t parity,
-                                                          const WaitCtx w) {
-  if (mbar_try_wait_acq_cluster(bar, parity)) return true;
-  const uint64_t t0 = global_timer_ns();
-  for (uint32_t spin = 1;; ++spin) {
-    if (mbar_try_wait_acq_cluster(bar, parity)) return true;
-    if ((spin & 15u) == 0) {
-      if (*w.abort_flag) return false;
-      if (global_timer_ns() - t0 > w.limit_ns) {
-        wait_fail(w, 5 /* PCC_ERR_TIMEOUT */);
-        return false;
-      }
-    }
-  }
-}
-
-// One segment of a CTA pair's range: tile pair t, passes [q0, q1).
-struct Segment {
-  int64_t t, q0, q1;
-};
-
-// The next segment of the range [u, u1) of (tile pair, pass) units, numbered
-// tile by tile.
-__device__ __forceinline__ Segment next_segment(int64_t u, int64_t u1,
-                                                int64_t npass) {
-  Segment g;
-  g.t = u / npass;
-  g.q0 = u - g.t * npass;
-  int64_t q1 = g.q0 + (u1 - u);
-  if (q1 > npass) q1 = npass;
-  if (q1 - g.q0 > kSMaxSegPasses) q1 = g.q0 + kSMaxSegPasses;
-  g.q1 = q1;
-  return g;
-}
 
 template <bool BF16>
 __global__ void __launch_bounds__(kSThreads, 1)

@@ -64,9 +64,11 @@ def test_allocation_failure_is_reported(pcc_gpu):
     assert pcc.pcc_sync_status(Z) == 0
 
 
+@pytest.mark.parametrize("form", [0, 2])
 @pytest.mark.parametrize("drop", [1, 2, 3])
-def test_perm_smem_wait_timeout_is_reported(pcc_gpu, drop):
-    """The shared-memory permutation form under the same hook: its A
+def test_perm_pair_form_wait_timeout_is_reported(pcc_gpu, drop, form):
+    """The permutation forms without a workspace under the same hook (0:
+    permuted in shared memory, 2: copied from a transposed Z): their A
     producer issues no loads (1), or only the even (2) / odd (3) CTA of
     each pair does; the waits run out, PCC_ERR_TIMEOUT is reported, and
     the next test gives the workspace form's counts."""
@@ -79,7 +81,7 @@ def test_perm_smem_wait_timeout_is_reported(pcc_gpu, drop):
     cnt = torch.zeros(n * (n - 1) // 2, dtype=torch.int32, device="cuda")
     before = pcc.pcc_get_tuning()
     try:
-        pcc.pcc_set_tuning(pair_mma=1, perm_workspace=0)
+        pcc.pcc_set_tuning(pair_mma=1, perm_workspace=form)
         pcc.pcc_set_wait_limit_ns(200_000_000)  # 0.2 s
         pcc.pcc_debug_drop_loads(drop)
         pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)

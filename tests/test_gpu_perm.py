@@ -121,9 +121,9 @@ def test_small_workspace_batches(pcc_gpu, tmp_path):
     assert np.array_equal(np.load(tmp_path / "g.npy"), whole)
 
 
-@pytest.mark.parametrize("workspace", [0, 1])
+@pytest.mark.parametrize("workspace", [0, 1, 2])
 def test_bad_permutation_index_is_reported(pcc_gpu, workspace):
-    """Both forms check every index: out of range is read as sample 0 and
+    """Every form checks every index: out of range is read as sample 0 and
     recorded; the other permutations' counts are unaffected."""
     X = synth.counts_log(200, 32, seed=5)
     perms = synth.fisher_yates_perms(4, 32, seed=6)
@@ -229,6 +229,7 @@ def test_perm_counts_long_rows(pcc_gpu, l):
     assert exact > 0.5 * total
 
 
+@pytest.mark.parametrize("form", [0, 2])
 @pytest.mark.parametrize("n,l,P,prec", [
     (300, 33, 41, "fp16x3s"),    # 3 tile columns: a dummy partner tile
     (520, 200, 40, "bf16x3"),    # 5 tile columns
@@ -237,11 +238,12 @@ def test_perm_counts_long_rows(pcc_gpu, l):
     (260, 96, 1, "fp16x3s"),     # one permutation: a lone pass only
     (700, 130, 2, "bf16x3"),     # one full pass per tile
 ])
-def test_perm_smem_equals_workspace(pcc_gpu, n, l, P, prec):
-    """CTA pairs that permute the column rows in shared memory give the
-    workspace form's counts exactly (same MMAs on the same operands),
-    including a column's lone last tile, an odd number of permutations, a
-    single permutation and resumed ranges that cut the pass sequence."""
+def test_perm_pair_forms_equal_workspace(pcc_gpu, n, l, P, prec, form):
+    """CTA pairs that permute the column rows in shared memory (form 0) or
+    copy them from a transposed Z (form 2) give the workspace form's counts
+    exactly (the same products on the same operands), including a column's
+    lone last tile, an odd number of permutations, a single permutation and
+    resumed ranges that cut the pass sequence."""
     pcc = pcc_gpu
     X = synth.counts_log(n, l, seed=3 * n + l)
     X[n // 4] = 0.5  # flagged row: counts stay 0
@@ -250,7 +252,7 @@ def test_perm_smem_equals_workspace(pcc_gpu, n, l, P, prec):
     try:
         pcc.pcc_set_tuning(pair_mma=1, perm_workspace=1)
         ref, st0, Z = gpu_perm_counts(pcc, X, perms, prec)
-        pcc.pcc_set_tuning(perm_workspace=0)
+        pcc.pcc_set_tuning(perm_workspace=form)
         got, st1, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z)
         cut = [(0, P // 3), (P // 3, P)] if P > 2 else [(0, 1), (1, P)]
         part, st2, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z,
@@ -267,11 +269,12 @@ def test_perm_smem_equals_workspace(pcc_gpu, n, l, P, prec):
     assert exact > 0.5 * tot
 
 
+@pytest.mark.parametrize("form", [0, 2])
 @pytest.mark.parametrize("n,l,pair", [(300, 64, 0), (260, 300, 1)])
-def test_perm_smem_switch_falls_back(pcc_gpu, n, l, pair):
-    """Where the shared-memory form does not apply (single CTAs, or rows
-    longer than 256 samples), selecting it runs the workspace form: the
-    counts equal the workspace form's."""
+def test_perm_pair_form_switch_falls_back(pcc_gpu, n, l, pair, form):
+    """Where a form without the workspace does not apply (single CTAs, or
+    rows longer than 256 samples), selecting it runs the workspace form:
+    the counts equal the workspace form's."""
     pcc = pcc_gpu
     X = synth.counts_log(n, l, seed=n + l)
     perms = synth.fisher_yates_perms(9, l, seed=l)
@@ -279,7 +282,7 @@ def test_perm_smem_switch_falls_back(pcc_gpu, n, l, pair):
     try:
         pcc.pcc_set_tuning(pair_mma=pair, perm_workspace=1)
         ref, st0, Z = gpu_perm_counts(pcc, X, perms, "bf16x3")
-        pcc.pcc_set_tuning(perm_workspace=0)
+        pcc.pcc_set_tuning(perm_workspace=form)
         got, st1, _ = gpu_perm_counts(pcc, X, perms, "bf16x3", Z=Z)
     finally:
         pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
