@@ -618,15 +618,15 @@ def run_perm(args):
     ms_graph = _graph_timed(step, max(3, min(args.steps, 20)), 1)
     ms = ms_graph if ms_graph is not None else ms_stream
     st = pcc.pcc_sync_status(Z)
-    # the forms without a workspace (0: permuted in shared memory, 2: copied
-    # from a transposed Z): their times, and the same counts
+    # the other forms (0: permuted in shared memory, 1: through a workspace
+    # of permuted rows): their times, and the same counts
     ref_cnt = cnt.clone()
     before = pcc.pcc_get_tuning()
     other = {}
     try:
         for form, name in ((0, "shared_memory_form"),
-                           (2, "transposed_copy_form")):
-            pcc.pcc_set_tuning(perm_workspace=form)
+                           (1, "workspace_form")):
+            pcc.pcc_set_tuning(perm_form=form)
             ms_f = _timed(step, 3, 1, stream)
             other[name] = {
                 "ms_per_step": ms_f,
@@ -634,7 +634,7 @@ def run_perm(args):
                 "status": pcc.pcc_sync_status(Z),
                 "value": n * (n - 1) / 2 * l * P / (ms_f / 1e3) / 1e9}
     finally:
-        pcc.pcc_set_tuning(perm_workspace=before["perm_workspace"])
+        pcc.pcc_set_tuning(perm_form=before["perm_form"])
     info = Z.info()
     tiles = (-(-n // 128)) * (-(-n // 128) + 1) // 2
     exec_flops = FORMS[info["prec"]][1] * 2 * 128 * 128 * info["lpad"] * tiles * (P + 1)
@@ -664,8 +664,8 @@ def run_perm(args):
                        "repeats r_obs per chunk of permutations and pads "
                        "lone tiles in the pair form (about 5% more tensor "
                        "work, not counted)"},
-           # the forms without the permuted workspace
-           # (pcc_set_perm_workspace(0) / (2)), stream-launched, 3 steps
+           # the other forms (pcc_set_perm_form(0) / (1)), stream-launched,
+           # 3 steps
            **other}
     print(json.dumps(out), flush=True)
     return 0

@@ -57,6 +57,17 @@ typedef enum {
 /* element type of an input or output array */
 typedef enum { PCC_F32 = 0, PCC_F64 = 1 } pcc_dtype;
 
+/* Forms of the permutation test (pcc_set_perm_form); all give the same
+ * counts. */
+typedef enum {
+    PCC_PERM_SMEM = 0,       /* CTA pairs permute resident rows in shared
+                                memory */
+    PCC_PERM_WORKSPACE = 1,  /* a gather launch writes permuted rows to a
+                                work buffer first */
+    PCC_PERM_TRANSPOSED = 2  /* CTA pairs copy permuted operands from a
+                                transposed copy of Z (the default) */
+} pcc_perm_form;
+
 /* how Z is stored and which pair kernel contracts it */
 typedef enum {
     PCC_PREC_FP64 = 0,    /* Z in FP64; FP64 CUDA-core pair kernel */
@@ -300,16 +311,21 @@ pcc_status pcc_edges_copy_host(const pcc_edge *edges, const uint64_t *d_count,
  *             (pcc_sync_status).  Whether a row is a permutation is not
  *             checked.
  *   d_counts  device uint32, n(n-1)/2, packed like R.
- * Two forms, with the same counts:
- *   - the workspace form (the default): the permuted rows of a batch of
- *     permutations are first written to a work buffer, allocated by the
- *     first such call on a Z and kept in Z (4.2 GB for 1,000 permutations
- *     of a 4,096 x 256 matrix; smaller budgets run in batches);
- *   - the shared-memory form (pcc_set_perm_workspace(0), CTA pairs, rows of
- *     up to 256 padded samples): each CTA keeps 64 of the column tile's
- *     rows z_j resident in shared memory and builds every permuted operand
- *     there; no device memory is allocated, at about 2.6 times the
- *     workspace form's time (shared-memory bandwidth).
+ * Three forms, with the same counts (pcc_set_perm_form):
+ *   - the transposed form (the default; CTA pairs, rows of up to 256 padded
+ *     samples): the first call after each standardize writes a transposed
+ *     copy of Z (2 x lpad x n 16-bit values, kept in Z), so that the
+ *     permuted column operand of a tile is a set of rows of that copy,
+ *     which the kernel copies from L2 into shared memory as it goes;
+ *   - the workspace form: the permuted rows of a batch of permutations are
+ *     first written to a work buffer, allocated by the first such call on a
+ *     Z and kept in Z (4.2 GB for 1,000 permutations of a 4,096 x 256
+ *     matrix; smaller budgets run in batches); about 1.2 times the
+ *     transposed form's time;
+ *   - the shared-memory form (CTA pairs, rows of up to 256 padded samples):
+ *     each CTA keeps 64 of the column tile's rows z_j resident in shared
+ *     memory and builds every permuted operand there; no device memory is
+ *     allocated, at about 3 times the transposed form's time.
  * Errors: PCC_ERR_INVALID_ARG for a bad range, NULL pointers or a non
  * tensor-core Z. */
 pcc_status pcc_perm_test(const pcc_zmat *Z, const int32_t *d_perms,
@@ -427,16 +443,15 @@ pcc_status pcc_set_tuning(int32_t stage_k, int32_t cluster, int32_t band_rows,
 pcc_status pcc_set_pair_mma(int32_t on);
 int32_t pcc_get_pair_mma(void);
 
-/* The form of pcc_perm_test.  on = 1 (the default; PCC_PERM_WORKSPACE=0 in
- * the environment selects 0 when the library loads): every call gathers
- * the permuted rows into a work buffer first; 0: CTA pairs permute the
- * column rows in shared memory wherever rows fit (padded length <= 256 and
- * pcc_set_pair_mma on), allocating nothing.  Affects later calls only; the
- * counts are the same.
- * Errors: PCC_ERR_INVALID_ARG unless on is 0 or 1.  The paper has no
+/* The form of pcc_perm_test (a pcc_perm_form; PCC_PERM_FORM=<0|1|2> in the
+ * environment sets it when the library loads).  PCC_PERM_TRANSPOSED (the
+ * default) and PCC_PERM_SMEM apply where rows fit (padded length <= 256),
+ * pcc_set_pair_mma is on and n > 128; elsewhere the workspace form runs.
+ * Affects later calls only; the counts are the same.
+ * Errors: PCC_ERR_INVALID_ARG unless form is 0, 1 or 2.  The paper has no
  * counterpart (a GB300 execution choice). */
-pcc_status pcc_set_perm_workspace(int32_t on);
-int32_t pcc_get_perm_workspace(void);
+pcc_status pcc_set_perm_form(int32_t form);
+int32_t pcc_get_perm_form(void);
 
 /* Current knob values (any pointer may be NULL). */
 pcc_status pcc_get_tuning(int32_t *stage_k, int32_t *cluster,

@@ -37,6 +37,9 @@ PCC_PREC_FP16X3S = 3
 PCC_PREC_BF16X4 = 4
 PCC_PREC_BF16X1 = 5
 PCC_PREC_AUTO = 6
+PCC_PERM_SMEM = 0
+PCC_PERM_WORKSPACE = 1
+PCC_PERM_TRANSPOSED = 2
 
 PREC_NAMES = {"fp64": PCC_PREC_FP64, "fp32": PCC_PREC_FP32,
               "bf16x3": PCC_PREC_BF16X3, "fp16x3s": PCC_PREC_FP16X3S,
@@ -122,8 +125,8 @@ def load(path: str | None = None):
         "pcc_set_pair_mma": (_ST, [_I32]),
         "pcc_measure_fp32_fma": (_ST, [_P, _P]),
         "pcc_get_pair_mma": (_I32, []),
-        "pcc_set_perm_workspace": (_ST, [_I32]),
-        "pcc_get_perm_workspace": (_I32, []),
+        "pcc_set_perm_form": (_ST, [_I32]),
+        "pcc_get_perm_form": (_I32, []),
         "pcc_num_pairs": (_I64, [_I64]),
         "pcc_pair_index": (_I64, [_I64, _I64, _I64]),
         "pcc_pair_coords": (_ST, [_I64, _I64, _P, _P]),
@@ -516,20 +519,20 @@ def pcc_debug_drop_loads(enable):
 
 
 def pcc_set_tuning(stage_k=0, cluster=0, band_rows=0, cost_c0=0.0,
-                   cost_c1=0.0, pair_mma=None, perm_workspace=None):
+                   cost_c1=0.0, pair_mma=None, perm_form=None):
     """Zeros (and None) keep a value; pair_mma 1/0 selects CTA pairs running
-    one 2-SM MMA or independent CTAs (pcc_set_pair_mma); perm_workspace
-    1 (the default) runs the permutation test through a workspace of
-    permuted rows, 0 lets CTA pairs permute them in shared memory where
-    rows fit, allocating nothing (pcc_set_perm_workspace)."""
+    one 2-SM MMA or independent CTAs (pcc_set_pair_mma); perm_form selects
+    the form of the permutation test (pcc_set_perm_form):
+    PCC_PERM_TRANSPOSED (the default), PCC_PERM_WORKSPACE or
+    PCC_PERM_SMEM."""
     _check(load().pcc_set_tuning(int(stage_k), int(cluster), int(band_rows),
                                  float(cost_c0), float(cost_c1)),
            "pcc_set_tuning")
     if pair_mma is not None:
         _check(load().pcc_set_pair_mma(int(pair_mma)), "pcc_set_pair_mma")
-    if perm_workspace is not None:
-        _check(load().pcc_set_perm_workspace(int(perm_workspace)),
-               "pcc_set_perm_workspace")
+    if perm_form is not None:
+        _check(load().pcc_set_perm_form(int(perm_form)),
+               "pcc_set_perm_form")
 
 
 def pcc_measure_fp32_fma(stream=None) -> float:
@@ -549,7 +552,7 @@ def pcc_get_tuning() -> dict:
     return dict(stage_k=k.value, cluster=c.value, band_rows=b.value,
                 cost_c0=c0.value, cost_c1=c1.value,
                 pair_mma=int(load().pcc_get_pair_mma()),
-                perm_workspace=int(load().pcc_get_perm_workspace()))
+                perm_form=int(load().pcc_get_perm_form()))
 
 
 def pcc_num_pairs(n: int) -> int:

@@ -114,11 +114,12 @@ TcTuning g_tune = [] {
   t.band = (v >= 1 && v <= 4096) ? v : 32;
   t.cost_c0 = 3000.0;
   t.cost_c1 = 260.0;
-  // the workspace form of the permutation test is the faster one; the
-  // shared-memory form is chosen with PCC_PERM_WORKSPACE=0
-  e = getenv("PCC_PERM_WORKSPACE");
-  const int pw = e ? atoi(e) : 1;
-  t.perm_workspace = (pw == 0 || pw == 2) ? pw : 1;
+  // the transposed form of the permutation test is the fastest one
+  e = getenv("PCC_PERM_FORM");
+  const int pf = e ? atoi(e) : PCC_PERM_TRANSPOSED;
+  t.perm_form = (pf == PCC_PERM_SMEM || pf == PCC_PERM_WORKSPACE)
+                    ? pf
+                    : PCC_PERM_TRANSPOSED;
   e = getenv("PCC_TC_ONEACC");
   const int oa = e ? atoi(e) : 0;
   t.one_acc_l = oa >= 64 ? oa : 1024;
@@ -152,6 +153,15 @@ void tc_set_tuning(const TcTuning& t) {
 cudaError_t ensure_func_smem(const void* func, int bytes) {
   return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               bytes);
+}
+
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown: treat as captured (rebuilding is always right)
+  }
+  return st != cudaStreamCaptureStatusNone;
 }
 
 pcc_status cuda_status(cudaError_t e) {
@@ -676,15 +686,17 @@ pcc_status pcc_set_pair_mma(int32_t on) {
 
 int32_t pcc_get_pair_mma(void) { return tc_tuning().pair_mma; }
 
-pcc_status pcc_set_perm_workspace(int32_t on) {
-  if (on < 0 || on > 2) return PCC_ERR_INVALID_ARG;
+pcc_status pcc_set_perm_form(int32_t form) {
+  if (form != PCC_PERM_SMEM && form != PCC_PERM_WORKSPACE &&
+      form != PCC_PERM_TRANSPOSED)
+    return PCC_ERR_INVALID_ARG;
   TcTuning t = tc_tuning();
-  t.perm_workspace = on;
+  t.perm_form = form;
   tc_set_tuning(t);
   return PCC_OK;
 }
 
-int32_t pcc_get_perm_workspace(void) { return tc_tuning().perm_workspace; }
+int32_t pcc_get_perm_form(void) { return tc_tuning().perm_form; }
 
 pcc_status pcc_get_tuning(int32_t* stage_k, int32_t* cluster,
                           int32_t* band_rows, double* cost_c0,

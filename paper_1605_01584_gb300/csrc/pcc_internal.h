@@ -63,6 +63,8 @@ uint64_t wait_limit_ns();
 // CTA of each pair, 3 the even CTA of each pair
 int debug_drop_loads();
 cudaError_t ensure_func_smem(const void* func, int bytes);
+// True while `s` is being captured into a CUDA graph.
+bool stream_capturing(cudaStream_t s);
 pcc_status cuda_status(cudaError_t e);
 
 // TMA descriptor of a 2-D row-major 16-bit matrix rows x cols (cols a
@@ -89,11 +91,7 @@ struct TcTuning {
   double cost_c1;    // batched plan: cycles per K block and product
   int64_t one_acc_l;  // padded rows up to this length use one accumulator
   int64_t chunk_l;    // longer rows: accumulator chunks of at most this
-  int perm_workspace;  // 1 (default): the permutation test gathers
-                       // permuted rows into a workspace; 0: CTA pairs
-                       // permute in shared memory where rows fit
-                       // (lpad <= 256); 2: CTA pairs copy permuted
-                       // operands from a transposed Z (lpad <= 256)
+  int perm_form;       // pcc_perm_form of the permutation test
 };
 TcTuning tc_tuning();
 void tc_set_tuning(const TcTuning& t);
@@ -174,13 +172,13 @@ pcc_status perm_test(pcc_zmat* Z, const int32_t* d_perms, int32_t P,
                      cudaStream_t s);
 // K6 on CTA pairs that permute the column rows in shared memory
 // (tc_perm_smem.cu): for rows of up to 256 padded samples, when the pair
-// form is on and the shared-memory form is selected (perm_workspace 0).
+// form is on and the shared-memory form is selected (perm_form PCC_PERM_SMEM).
 bool perm_smem_applies(const pcc_zmat* Z);
 pcc_status perm_test_smem(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
                           int32_t k1, uint32_t* d_counts, cudaStream_t s);
 // K6 on CTA pairs that copy the permuted column operand from a transposed
 // copy of Z (tc_perm_mn.cu): rows of up to 256 padded samples, pair form on,
-// perm_workspace 2.
+// perm_form PCC_PERM_TRANSPOSED.
 bool perm_mn_applies(const pcc_zmat* Z);
 pcc_status perm_test_mn(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
                         int32_t k1, uint32_t* d_counts, cudaStream_t s);

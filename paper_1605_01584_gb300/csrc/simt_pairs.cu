@@ -472,7 +472,8 @@ int64_t km_npad(int64_t n) { return (n + kKmBT - 1) / kKmBT * kKmBT; }
 // standardize entry points clear zt_valid); kept in Z.
 cudaError_t ensure_zt(const pcc_zmat* Zc, cudaStream_t s) {
   pcc_zmat* Z = const_cast<pcc_zmat*>(Zc);
-  if (Z->zt_valid) return cudaSuccess;
+  // a captured call transposes again: its replay may follow a standardize
+  if (Z->zt_valid && !stream_capturing(s)) return cudaSuccess;
   const int64_t npad = km_npad(Z->n);
   const size_t need = (size_t)npad * (size_t)Z->lpad * sizeof(float);
   if (Z->zt_bytes < need) {

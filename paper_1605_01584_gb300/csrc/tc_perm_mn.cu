@@ -21,16 +21,17 @@
 // tile, are cut into one contiguous range per CTA pair; a tile's passes are
 // a segment with one r_obs pass.
 //
-// Roles (10 warps): warp 0 loads each segment's A tile and forwards every
+// Roles (12 warps): warp 0 loads each segment's A tile and forwards every
 // filled B stage to the even CTA's MMA; warp 1 (lane 0 of the even CTA)
-// issues the MMAs; warps 2-9 copy B stages (8 chunks per thread and stage,
-// completion counted by cp.async.mbarrier.arrive on this CTA's barrier, so
-// no thread waits for its copies) and, after a pass's copies, read the
-// accumulator of the previous pass (|r_obs| and 16-bit counts in registers,
-// one atomic per pair and segment).  Every wait is bounded.
+// issues the MMAs; warps 2-3 copy B stages (KP/4 samples x 2 halves per
+// thread and stage, completion counted by cp.async.mbarrier.arrive on this
+// CTA's barrier, so no thread waits for its copies); warps 4-11 read the
+// accumulator of each pass (|r_obs| and 16-bit counts in registers, one
+// atomic per pair and segment).  Every wait is bounded.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "pcc_internal.h"
 #include "pcc_ptx.cuh"
@@ -41,20 +42,30 @@
 namespace pcc {
 namespace {
 
-constexpr int kMThreads = 320;                 // 10 warps
-constexpr int kMKP = 64;                       // samples per stage
-constexpr int kMTile = kPT * kMKP * 2;         // 128 rows x 64 x 16 bit
-constexpr int kMABytes = (kPMaxResidentK / kMKP) * 2 * kMTile;  // 128 KB
-constexpr int kMStages = 3;
-constexpr int kMStageBytes = 2 * kMTile;       // [B hi | B lo], MN-major
+constexpr int kMCopyWarps = 2;
+constexpr int kMCopiers = kMCopyWarps * 32;       // copying threads per CTA
+constexpr int kMEpi0 = 2 + kMCopyWarps;           // first epilogue warp
+constexpr int kMThreads = (kMEpi0 + kPEpiWarps) * 32;  // 12 warps
+constexpr int kMATile = kPT * 64 * 2;             // A: 128 rows x 64 x 16 bit
+constexpr int kMABytes = (kPMaxResidentK / 64) * 2 * kMATile;  // 128 KB
+constexpr int kMRing = 96 * 1024;                 // B stages
 constexpr int kMBarBytes = 512;
-constexpr int kMSmemBytes =
-    1024 + kMABytes + kMStages * kMStageBytes + kMBarBytes;
+constexpr int kMSmemBytes = 1024 + kMABytes + kMRing + kMBarBytes;
 static_assert(kMSmemBytes <= kPSmemBudget, "shared memory");
-constexpr int kMWorkers = kPEpiWarps * 32;     // copying threads per CTA
 // MN-major B: gene atoms (64 genes) 1 KB apart, 8-sample groups 2 KB apart
 constexpr uint32_t kMLbo = 1024, kMSbo = 2048;
-static_assert(kMTile == (kMKP / 8) * kMSbo, "B layout");
+
+// B stages of KP samples: [hi | lo], each 128 genes x KP samples
+template <int KP>
+struct MnStage {
+  static constexpr int kTile = kPT * KP * 2;
+  static constexpr int kBytes = 2 * kTile;
+  static constexpr int kStages = kMRing / kBytes;
+  static constexpr int kPer = KP / 4;  // samples per copying thread
+  static_assert(kTile == (KP / 8) * (int)kMSbo, "B layout");
+  static_assert(kPer * 4 * 16 == KP * 16 && kMCopiers == 64, "copy share");
+  static_assert(kStages <= 6, "barrier area");
+};
 
 struct PermMnParams {
   int64_t n;
@@ -66,7 +77,7 @@ struct PermMnParams {
   int64_t l;
   int64_t lpad;
   int64_t npad;       // row length of ZT (genes, a multiple of 128)
-  int nkb;            // stages per pass: lpad / 64
+  int nkb;            // B stages per pass: lpad / KP
   int lolo;           // 1: the fourth product lo.lo (BF16X4)
   const int32_t* perms;   // permutation k at perms + k * l
   const uint16_t* zt_hi;  // ZT halves, lpad x npad
@@ -98,6 +109,14 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
 
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// A read-only 32-bit load issued where it stands in program order (before
+// a wait that follows it), so that its latency overlaps the wait.
+__device__ __forceinline__ int32_t ld_nc_s32(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
 }
 
 // Shared-memory descriptor of an MN-major operand with 128-byte swizzle:
@@ -136,11 +155,13 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <bool BF16>
+template <bool BF16, int KP>
 __global__ void __launch_bounds__(kMThreads, 1)
     k_perm_mn(const __grid_constant__ CUtensorMap tz_hi,
               const __grid_constant__ CUtensorMap tz_lo,
               const PermMnParams p) {
+  using St = MnStage<KP>;
+  constexpr int S = St::kStages;
   // M = 256 (both CTAs' tiles), N = 256 (128 genes from each CTA), A
   // K-major, B MN-major (bit 16 of the instruction descriptor)
   constexpr uint32_t kIdesc =
@@ -151,14 +172,13 @@ __global__ void __launch_bounds__(kMThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t* aregion = smem;                   // resident A: [kb][hi | lo]
+  uint8_t* aregion = smem;                   // resident A: [64 samples][hi|lo]
   uint8_t* ring = smem + kMABytes;           // B stages: [hi | lo]
-  uint64_t* bars =
-      reinterpret_cast<uint64_t*>(ring + kMStages * kMStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kMRing);
   uint64_t* full = bars;                     // even CTA: both forwards
-  uint64_t* empty = bars + kMStages;         // the MMA's commit, both CTAs
-  uint64_t* bfull = bars + 2 * kMStages;     // this CTA's copies landed
-  uint64_t* tfull = bars + 3 * kMStages;
+  uint64_t* empty = bars + 6;                // the MMA's commit, both CTAs
+  uint64_t* bfull = bars + 12;               // this CTA's copies landed
+  uint64_t* tfull = bars + 18;
   uint64_t* tempty = tfull + 2;
   uint64_t* afull = tempty + 2;
   uint64_t* aempty = afull + 1;
@@ -166,21 +186,21 @@ __global__ void __launch_bounds__(kMThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mdone + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   FillLog* flog = reinterpret_cast<FillLog*>(bars + 32);  // A copies
-  static_assert(3 * kMStages + 7 <= 31, "barrier area");
+  static_assert(18 + 7 <= 31, "barrier area");
   static_assert(32 * 8 + sizeof(FillLog) <= kMBarBytes, "barrier area");
 
-  auto sA_hi = [&](int kb) { return aregion + kb * 2 * kMTile; };
-  auto sA_lo = [&](int kb) { return sA_hi(kb) + kMTile; };
-  auto sB_hi = [&](int s) { return ring + s * kMStageBytes; };
-  auto sB_lo = [&](int s) { return sB_hi(s) + kMTile; };
+  auto sA_hi = [&](int a) { return aregion + a * 2 * kMATile; };
+  auto sA_lo = [&](int a) { return sA_hi(a) + kMATile; };
+  auto sB_hi = [&](int s) { return ring + s * St::kBytes; };
+  auto sB_lo = [&](int s) { return sB_hi(s) + St::kTile; };
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kMStages; ++s) {
-      mbar_init(&full[s], 2);           // the forwarder of each CTA
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 2);          // the forwarder of each CTA
       mbar_init(&empty[s], 1);
-      mbar_init(&bfull[s], kMWorkers);  // every copying thread, no-inc
+      mbar_init(&bfull[s], kMCopiers);  // every copying thread, no-inc
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -230,7 +250,8 @@ __global__ void __launch_bounds__(kMThreads, 1)
     if (lane == 0) {
       // ---------------------------------- A tiles and stage forwarding
       const uint64_t pol = l2_policy_evict_last();
-      const uint32_t abytes = (uint32_t)(p.nkb * 2 * kMTile);
+      const int na = (int)(p.lpad / 64);
+      const uint32_t abytes = (uint32_t)(na * 2 * kMATile);
       const uint32_t full0 = cluster_addr(&full[0], 0);  // the even CTA's
       uint32_t aph = 0;
       int stage = 0;
@@ -248,9 +269,9 @@ __global__ void __launch_bounds__(kMThreads, 1)
         // both CTAs' A tiles count on the even CTA's barrier
         if (crank == 0) mbar_arrive_expect_tx(afull, 2u * abytes);
         const uint32_t ab = cluster_addr(afull, 0);
-        for (int kb = 0; kb < p.nkb; ++kb) {
-          tma_load_2d_pair(sA_hi(kb), &tz_hi, ab, kb * kMKP, (int)row0, pol);
-          tma_load_2d_pair(sA_lo(kb), &tz_lo, ab, kb * kMKP, (int)row0, pol);
+        for (int a = 0; a < na; ++a) {
+          tma_load_2d_pair(sA_hi(a), &tz_hi, ab, a * 64, (int)row0, pol);
+          tma_load_2d_pair(sA_lo(a), &tz_lo, ab, a * 64, (int)row0, pol);
         }
         aph ^= 1u;
         // each B stage this CTA's copies filled goes to the MMA issuer:
@@ -265,7 +286,7 @@ __global__ void __launch_bounds__(kMThreads, 1)
           fence_proxy_async_smem();
           fence_release_smem_cluster();
           mbar_arrive_relaxed_cluster(full0 + (uint32_t)(stage * 8));
-          if (++stage == kMStages) {
+          if (++stage == S) {
             stage = 0;
             phase ^= 1u;
           }
@@ -301,12 +322,16 @@ __global__ void __launch_bounds__(kMThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t aH = smem_u32(sA_hi(kb));
-            const uint32_t aL = smem_u32(sA_lo(kb));
+            // samples kb*KP.. of the A tiles: tile (kb*KP)/64, at byte
+            // 2 ((kb*KP) mod 64) of its 128-byte rows
+            const int a = (kb * KP) >> 6;
+            const uint32_t aoff = (uint32_t)(((kb * KP) & 63) * 2);
+            const uint32_t aH = smem_u32(sA_hi(a)) + aoff;
+            const uint32_t aL = smem_u32(sA_lo(a)) + aoff;
             const uint32_t bH = smem_u32(sB_hi(stage));
             const uint32_t bL = smem_u32(sB_lo(stage));
 #pragma unroll
-            for (int ks = 0; ks < kMKP / kPUK; ++ks) {
+            for (int ks = 0; ks < KP / kPUK; ++ks) {
               // A: +32 B per 16 samples inside its 128-byte rows; B: two
               // 8-sample groups per 16 samples
               const uint64_t dAH = kmajor_desc<128>(aH + ks * kPUK * 2);
@@ -319,7 +344,7 @@ __global__ void __launch_bounds__(kMThreads, 1)
               if (p.lolo) umma_f16_pair(d_tmem, dAL, dBL, kIdesc, 1u);
             }
             umma_commit_pair(&empty[stage], 3);  // frees it in both CTAs
-            if (++stage == kMStages) {
+            if (++stage == S) {
               stage = 0;
               phase ^= 1u;
             }
@@ -337,34 +362,29 @@ __global__ void __launch_bounds__(kMThreads, 1)
       wd.abort_flag = &never;
       mbar_wait(mdone, 0, wd);
     }
-  } else {
-    // ------------------------------------------------- copies and epilogue
-    // Each worker copies its 8 chunks of every B stage, in stage order, and
-    // reads its accumulator quarter after each pass: pass pi: copy pi's
-    // stages, then the epilogue of pass pi - 1 (the MMA of pass pi needs
-    // only epilogue pi - 2, so the order cannot stall it).
-    const int q = warp & 3;          // TMEM lane quarter: rows 32q..32q+31
-    const int h = (warp - 2) >> 2;   // genes 64h..64h+63: columns 64h..
-    const int t = threadIdx.x - 64;  // copy share
-    const int sr = t >> 4;           // samples sr + 16j of each stage
-    const int cch = t & 15;          // genes 8cch..8cch+7 of the tile
-    // this thread's byte offset in a stage's B tile (128-byte swizzle:
-    // 8-sample group, gene atom, sample row, 16-byte chunk ^ row); sample
-    // sr + 16 j sits at + 4096 j
-    const uint32_t d0 = (uint32_t)((sr >> 3) * kMSbo + (cch >> 3) * kMLbo +
-                                   (sr & 7) * 128 +
-                                   (((cch & 7) ^ (sr & 7)) << 4));
+  } else if (warp < kMEpi0) {
+    // ------------------------------------------------------- B copies
+    // Thread t copies, for samples sr + 4i of a stage (i < KP/4), the 16
+    // bytes of genes 8c..8c+7 of both halves.  The permutation indices of
+    // a stage are loaded before its wait for a free slot.
+    const int t = threadIdx.x - 64;
+    const int sr = t >> 4;  // 0..3
+    const int cch = t & 15;
+    // byte offset of sample sr + 4i in a stage's tile: 8-sample group i/2,
+    // gene atom cch/8, row sr + 4 (i & 1) of the atom, chunk (cch & 7) ^ row
+    uint32_t dbase[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int r = sr + 4 * b;
+      dbase[b] = (uint32_t)((cch >> 3) * (int)kMLbo + r * 128 +
+                            (((cch & 7) ^ r) << 4));
+    }
     const int l = (int)p.l;
     const uint32_t npad = (uint32_t)p.npad;
     int stage = 0;
     uint32_t phase = 0;
-    int acc = 0;
-    uint32_t aphase = 0;
     bool ok = true;
     bool bad = false;
-    // element offsets (row of ZT) of this thread's 16 samples of a pass:
-    // row pi_k[s] for s < l, the (zero) padding row s itself otherwise
-    uint32_t rowoff[16];
     for (int64_t u = u_begin; u < u_end && ok;) {
       const Segment g = next_segment(u, u_end, p.npass);
       u += g.q1 - g.q0;
@@ -372,70 +392,75 @@ __global__ void __launch_bounds__(kMThreads, 1)
       seg_coords(g, &row0, &col0);
       const uint16_t* src_hi = p.zt_hi + col0 + 8 * cch;
       const uint16_t* src_lo = p.zt_lo + col0 + 8 * cch;
-      auto load_pass = [&](int64_t pi) {
+      const int64_t nps = g.q1 - g.q0;
+      for (int64_t pi = -1; pi < nps && ok; ++pi) {
         // the even CTA takes permutation k, the odd one k + 1 (a lone last
-        // permutation: k in both); pi < 0: the identity (r_obs)
+        // permutation: k in both); pi < 0: the identity (r_obs); a padding
+        // sample s >= l reads the (zero) row s itself
         const int64_t k0 = 2 * (g.q0 + pi);
         const int64_t k =
             k0 + (int64_t)crank < p.P ? k0 + (int64_t)crank : k0;
-        const int32_t* pr = p.perms + (p.kbase + k) * p.l;
+        const int32_t* pr = p.perms + (p.kbase + (pi < 0 ? 0 : k)) * p.l;
+        for (int kb = 0; kb < p.nkb; ++kb) {
+          int32_t v[St::kPer];
 #pragma unroll
-        for (int kb = 0; kb < kPMaxResidentK / kMKP; ++kb) {
+          for (int i = 0; i < St::kPer; ++i) {
+            const int s = kb * KP + sr + 4 * i;
+            v[i] = (pi >= 0 && s < l) ? ld_nc_s32(pr + s) : s;
+          }
+          bool okw = true;
+          if (lane == 0) okw = mbar_wait(&empty[stage], phase ^ 1u, w);
+          if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sb = smem_u32(sB_hi(stage));
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int s = kb * kMKP + sr + 16 * j;
-            int32_t v = s;
-            if (pi >= 0 && kb < p.nkb && s < l) {
-              v = __ldg(pr + s);
-              if ((uint32_t)v >= (uint32_t)l) {  // recorded, read as 0
-                bad = true;
-                v = 0;
-              }
+          for (int i = 0; i < St::kPer; ++i) {
+            const int s = kb * KP + sr + 4 * i;
+            int32_t r = v[i];
+            if (pi >= 0 && s < l && (uint32_t)r >= (uint32_t)l) {
+              bad = true;  // recorded, read as sample 0
+              r = 0;
             }
-            rowoff[kb * 4 + j] = (uint32_t)v * npad;
+            const uint32_t off = (uint32_t)r * npad;
+            const uint32_t dst =
+                sb + (uint32_t)((i >> 1) * (int)kMSbo) + dbase[i & 1];
+            cp_async16_cg(dst, src_hi + off);
+            cp_async16_cg(dst + (uint32_t)St::kTile, src_lo + off);
+          }
+          // counted on this CTA's barrier once they have landed
+          cp_async_arrive_noinc(&bfull[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
           }
         }
-      };
-      load_pass(-1);
+      }
+    }
+    if (bad) atomicCAS(p.status, 0, (int)PCC_ERR_INVALID_ARG);
+    // no copy of this thread may still be in flight when the CTA leaves
+    cp_async_wait_all();
+  } else {
+    // ----------------------------------------------------------- epilogue
+    const int q = warp & 3;               // TMEM lane quarter: rows 32q..
+    const int h = (warp - kMEpi0) >> 2;   // genes 64h..: columns 64h..
+    int acc = 0;
+    uint32_t aphase = 0;
+    bool ok = true;
+    for (int64_t u = u_begin; u < u_end && ok;) {
+      const Segment g = next_segment(u, u_end, p.npass);
+      u += g.q1 - g.q0;
+      int64_t row0, col0;
+      seg_coords(g, &row0, &col0);
       const int64_t nps = g.q1 - g.q0;
       float robs[64];
       uint32_t cnt[32];  // two 16-bit counts per word
 #pragma unroll
       for (int i = 0; i < 32; ++i) cnt[i] = 0u;
-      for (int64_t pi = -1; pi <= nps && ok; ++pi) {
-        if (pi < nps) {
-          // (a) the copies of pass pi
-#pragma unroll
-          for (int kb = 0; kb < kPMaxResidentK / kMKP; ++kb) {
-            if (kb >= p.nkb || !ok) break;
-            bool okw = true;
-            if (lane == 0) okw = mbar_wait(&empty[stage], phase ^ 1u, w);
-            if (!__shfl_sync(0xffffffffu, okw ? 1 : 0, 0)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sb = smem_u32(sB_hi(stage)) + d0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              cp_async16_cg(sb + (uint32_t)(j * 2 * kMSbo),
-                            src_hi + rowoff[kb * 4 + j]);
-              cp_async16_cg(sb + (uint32_t)(kMTile + j * 2 * kMSbo),
-                            src_lo + rowoff[kb * 4 + j]);
-            }
-            // counted on this CTA's barrier once they have landed
-            cp_async_arrive_noinc(&bfull[stage]);
-            if (++stage == kMStages) {
-              stage = 0;
-              phase ^= 1u;
-            }
-          }
-          if (!ok) break;
-          if (pi + 1 < nps) load_pass(pi + 1);
-        }
-        if (pi < 0) continue;
-        // (b) the epilogue of pass pe = pi - 1 (pe < 0: r_obs); permutation
-        // e of the pass at columns 128e + 64h..
-        const int64_t pe = pi - 1;
+      for (int64_t pe = -1; pe < nps; ++pe) {
+        // pass pe (pe < 0: r_obs); permutation e of the pass at columns
+        // 128e + 64h..
         const int nperm =
             pe < 0 ? 1 : (2 * (g.q0 + pe) + 1 < p.P ? 2 : 1);
         bool got = true;
@@ -493,9 +518,6 @@ __global__ void __launch_bounds__(kMThreads, 1)
         }
       }
     }
-    if (bad) atomicCAS(p.status, 0, (int)PCC_ERR_INVALID_ARG);
-    // no copy of this thread may still be in flight when the CTA leaves
-    cp_async_wait_all();
   }
 
   tc_fence_before();
@@ -510,9 +532,10 @@ __global__ void __launch_bounds__(kMThreads, 1)
 }
 
 // ZT (both halves, lpad x npad each) for the current contents of Z: built
-// on the first call after each standardize.
+// on the first call after each standardize, and by every call that a stream
+// capture records (a replay may follow a later standardize).
 cudaError_t ensure_zt16(pcc_zmat* Z, int64_t npad, cudaStream_t s) {
-  if (Z->zt_valid) return cudaSuccess;
+  if (Z->zt_valid && !stream_capturing(s)) return cudaSuccess;
   const size_t need = 2 * (size_t)npad * (size_t)Z->lpad * sizeof(uint16_t);
   if (Z->zt_bytes < need) {
     if (Z->zt) {
@@ -535,10 +558,10 @@ cudaError_t ensure_zt16(pcc_zmat* Z, int64_t npad, cudaStream_t s) {
   return e;
 }
 
-template <bool BF16>
+template <bool BF16, int KP>
 cudaError_t launch_mn(const pcc_zmat* Z, const PermMnParams& p,
                       cudaStream_t s) {
-  auto fn = k_perm_mn<BF16>;
+  auto fn = k_perm_mn<BF16, KP>;
   cudaError_t e =
       ensure_func_smem(reinterpret_cast<const void*>(fn), kMSmemBytes);
   if (e != cudaSuccess) return e;
@@ -575,19 +598,30 @@ cudaError_t launch_mn(const pcc_zmat* Z, const PermMnParams& p,
 
 int64_t mn_npad(int64_t n) { return (n + kPT - 1) / kPT * kPT; }
 
+// samples per B stage: 64 (three stages) or, with PCC_PERM_MN_K=32, 32
+// (six stages of half the size)
+int mn_stage_k() {
+  static const int k = [] {
+    const char* e = getenv("PCC_PERM_MN_K");
+    return (e && atoi(e) == 32) ? 32 : 64;
+  }();
+  return k;
+}
+
 }  // namespace
 
 bool perm_mn_applies(const pcc_zmat* Z) {
   const int64_t m = (Z->n + kPT - 1) / kPT;
   // ZT offsets of a sample row are 32-bit element offsets
   return Z->lpad <= kPMaxResidentK && m >= 2 && tc_tuning().pair_mma != 0 &&
-         tc_tuning().perm_workspace == 2 &&
+         tc_tuning().perm_form == PCC_PERM_TRANSPOSED &&
          (uint64_t)Z->lpad * (uint64_t)mn_npad(Z->n) < (1ull << 32);
 }
 
 pcc_status perm_test_mn(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
                         int32_t k1, uint32_t* d_counts, cudaStream_t s) {
   const int64_t n = Z->n;
+  const int kp = mn_stage_k();
   PermMnParams p;
   p.n = n;
   p.m = (n + kPT - 1) / kPT;
@@ -598,7 +632,7 @@ pcc_status perm_test_mn(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
   p.l = Z->l;
   p.lpad = Z->lpad;
   p.npad = mn_npad(n);
-  p.nkb = (int)(Z->lpad / kMKP);
+  p.nkb = (int)(Z->lpad / kp);
   p.lolo = Z->prec == PCC_PREC_BF16X4 ? 1 : 0;
   p.perms = d_perms;
   p.flags = Z->flags;
@@ -615,8 +649,11 @@ pcc_status perm_test_mn(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,
   p.zt_hi = static_cast<const uint16_t*>(Z->zt);
   p.zt_lo = p.zt_hi + (size_t)p.lpad * (size_t)p.npad;
   const bool bf16 = Z->prec != PCC_PREC_FP16X3S;
-  const cudaError_t e =
-      bf16 ? launch_mn<true>(Z, p, s) : launch_mn<false>(Z, p, s);
+  cudaError_t e;
+  if (kp == 32)
+    e = bf16 ? launch_mn<true, 32>(Z, p, s) : launch_mn<false, 32>(Z, p, s);
+  else
+    e = bf16 ? launch_mn<true, 64>(Z, p, s) : launch_mn<false, 64>(Z, p, s);
   return cuda_status(e);
 }
 

@@ -556,7 +556,7 @@ cudaError_t launch_smem(const pcc_zmat* Z, const PermSmemParams& p,
 bool perm_smem_applies(const pcc_zmat* Z) {
   const int64_t m = (Z->n + kPT - 1) / kPT;
   return Z->lpad <= kPMaxResidentK && m >= 2 && tc_tuning().pair_mma != 0 &&
-         tc_tuning().perm_workspace == 0;
+         tc_tuning().perm_form == PCC_PERM_SMEM;
 }
 
 pcc_status perm_test_smem(pcc_zmat* Z, const int32_t* d_perms, int32_t k0,

@@ -3,6 +3,7 @@ include/pcc.h declares, and its host numbering helpers (the closed forms of
 Eq. (14)-(15) and (17)-(19) with integer correction, the code the kernels
 also run) agree with the oracle's search-based numbering."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -84,16 +85,19 @@ def test_invalid_numbering_args(lib):
 
 def test_tuning_knobs_round_trip(lib):
     before = pcc.pcc_get_tuning()
+    if "PCC_PERM_FORM" not in os.environ:
+        assert before["perm_form"] == pcc.PCC_PERM_TRANSPOSED
     try:
         pcc.pcc_set_tuning(stage_k=64, cluster=1, band_rows=7, cost_c0=11.0,
-                           cost_c1=3.0, pair_mma=0, perm_workspace=0)
+                           cost_c1=3.0, pair_mma=0, perm_form=0)
         t = pcc.pcc_get_tuning()
         assert t == dict(stage_k=64, cluster=1, band_rows=7, cost_c0=11.0,
-                         cost_c1=3.0, pair_mma=0, perm_workspace=0)
+                         cost_c1=3.0, pair_mma=0, perm_form=0)
         pcc.pcc_set_tuning()  # zeros keep every value
         assert pcc.pcc_get_tuning() == t
         for bad in (dict(stage_k=48), dict(cluster=3), dict(band_rows=-2),
-                    dict(pair_mma=2), dict(perm_workspace=-1)):
+                    dict(pair_mma=2), dict(perm_form=-1),
+                    dict(perm_form=3)):
             with pytest.raises(pcc.PccError):
                 pcc.pcc_set_tuning(**bad)
         assert pcc.pcc_get_tuning() == t
@@ -101,4 +105,4 @@ def test_tuning_knobs_round_trip(lib):
         pcc.pcc_set_tuning(before["stage_k"], before["cluster"],
                            before["band_rows"], before["cost_c0"],
                            before["cost_c1"], before["pair_mma"],
-                           before["perm_workspace"])
+                           before["perm_form"])

@@ -81,7 +81,7 @@ def test_perm_pair_form_wait_timeout_is_reported(pcc_gpu, drop, form):
     cnt = torch.zeros(n * (n - 1) // 2, dtype=torch.int32, device="cuda")
     before = pcc.pcc_get_tuning()
     try:
-        pcc.pcc_set_tuning(pair_mma=1, perm_workspace=form)
+        pcc.pcc_set_tuning(pair_mma=1, perm_form=form)
         pcc.pcc_set_wait_limit_ns(200_000_000)  # 0.2 s
         pcc.pcc_debug_drop_loads(drop)
         pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
@@ -93,7 +93,7 @@ def test_perm_pair_form_wait_timeout_is_reported(pcc_gpu, drop, form):
         pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
         assert pcc.pcc_sync_status(Z) == 0
         got = cnt.cpu().numpy()
-        pcc.pcc_set_tuning(perm_workspace=1)
+        pcc.pcc_set_tuning(perm_form=1)
         cnt.zero_()
         pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
         assert pcc.pcc_sync_status(Z) == 0
@@ -101,7 +101,7 @@ def test_perm_pair_form_wait_timeout_is_reported(pcc_gpu, drop, form):
         pcc.pcc_debug_drop_loads(False)
         pcc.pcc_set_wait_limit_ns(4_000_000_000)
         pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
-                           perm_workspace=before["perm_workspace"])
+                           perm_form=before["perm_form"])
     ref = cnt.cpu().numpy()
     assert ref.max() > 0
     assert np.array_equal(got, ref)

@@ -114,7 +114,7 @@ def test_small_workspace_batches(pcc_gpu, tmp_path):
                                  str(tmp_path / "g.npy")))
     per_k = 260 * 128 * 4
     env = dict(os.environ, PCC_PERM_WS_BYTES=str(3 * per_k),
-               PCC_PERM_WORKSPACE="1")
+               PCC_PERM_FORM="1")
     r = subprocess.run([sys.executable, "-c", code], env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -132,11 +132,11 @@ def test_bad_permutation_index_is_reported(pcc_gpu, workspace):
     perms[3, 0] = -1
     before = pcc_gpu.pcc_get_tuning()
     try:
-        pcc_gpu.pcc_set_tuning(perm_workspace=workspace)
+        pcc_gpu.pcc_set_tuning(perm_form=workspace)
         got, st, _ = gpu_perm_counts(pcc_gpu, X, perms, ranges=[(0, 2)])
         _, st2, _ = gpu_perm_counts(pcc_gpu, X, perms)
     finally:
-        pcc_gpu.pcc_set_tuning(perm_workspace=before["perm_workspace"])
+        pcc_gpu.pcc_set_tuning(perm_form=before["perm_form"])
     assert st0 == 0 and st == 0
     assert np.array_equal(got, good)
     assert st2 == pcc_gpu.PCC_ERR_INVALID_ARG
@@ -250,16 +250,16 @@ def test_perm_pair_forms_equal_workspace(pcc_gpu, n, l, P, prec, form):
     perms = synth.fisher_yates_perms(P, l, seed=P + l)
     before = pcc.pcc_get_tuning()
     try:
-        pcc.pcc_set_tuning(pair_mma=1, perm_workspace=1)
+        pcc.pcc_set_tuning(pair_mma=1, perm_form=1)
         ref, st0, Z = gpu_perm_counts(pcc, X, perms, prec)
-        pcc.pcc_set_tuning(perm_workspace=form)
+        pcc.pcc_set_tuning(perm_form=form)
         got, st1, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z)
         cut = [(0, P // 3), (P // 3, P)] if P > 2 else [(0, 1), (1, P)]
         part, st2, _ = gpu_perm_counts(pcc, X, perms, prec, Z=Z,
                                        ranges=[r for r in cut if r[1] > r[0]])
     finally:
         pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
-                           perm_workspace=before["perm_workspace"])
+                           perm_form=before["perm_form"])
     assert st0 == st1 == st2 == 0
     assert ref.max() > 0
     assert np.array_equal(got, ref)
@@ -280,13 +280,56 @@ def test_perm_pair_form_switch_falls_back(pcc_gpu, n, l, pair, form):
     perms = synth.fisher_yates_perms(9, l, seed=l)
     before = pcc.pcc_get_tuning()
     try:
-        pcc.pcc_set_tuning(pair_mma=pair, perm_workspace=1)
+        pcc.pcc_set_tuning(pair_mma=pair, perm_form=1)
         ref, st0, Z = gpu_perm_counts(pcc, X, perms, "bf16x3")
-        pcc.pcc_set_tuning(perm_workspace=form)
+        pcc.pcc_set_tuning(perm_form=form)
         got, st1, _ = gpu_perm_counts(pcc, X, perms, "bf16x3", Z=Z)
     finally:
         pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
-                           perm_workspace=before["perm_workspace"])
+                           perm_form=before["perm_form"])
     assert st0 == st1 == 0
     assert ref.max() > 0
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_perm_graph_replay_follows_restandardize(pcc_gpu, form):
+    """A captured permutation test, replayed after Z was standardized again
+    from other data outside the graph, counts the new data: the transposed
+    form rebuilds its copy of Z inside every captured call."""
+    import torch
+    pcc = pcc_gpu
+    n, l, P = 300, 64, 6
+    d1 = torch.from_numpy(synth.counts_log(n, l, seed=11)).cuda()
+    d2 = torch.from_numpy(synth.counts_log(n, l, seed=12)).cuda()
+    perms = torch.from_numpy(synth.fisher_yates_perms(P, l, seed=13)).cuda()
+    cnt = torch.zeros(n * (n - 1) // 2, dtype=torch.int32, device="cuda")
+    before = pcc.pcc_get_tuning()
+    try:
+        pcc.pcc_set_tuning(pair_mma=1, perm_form=form)
+        Z = pcc.pcc_standardize(d2, "bf16x3")
+        pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)
+        want = cnt.cpu().numpy().copy()
+        pcc.pcc_standardize(d1, "bf16x3", Z=Z)
+        cnt.zero_()
+        pcc.pcc_perm_test(Z, perms, P, 0, P, cnt)  # the copy of d1 is built
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                pcc.pcc_perm_test(Z, perms, P, 0, P, cnt, stream=s)
+        torch.cuda.synchronize()
+        pcc.pcc_standardize(d2, "bf16x3", Z=Z)
+        torch.cuda.synchronize()
+        cnt.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        st = pcc.pcc_sync_status(Z)
+    finally:
+        pcc.pcc_set_tuning(pair_mma=before["pair_mma"],
+                           perm_form=before["perm_form"])
+    assert st == 0
+    assert want.max() > 0
+    assert np.array_equal(cnt.cpu().numpy(), want)
