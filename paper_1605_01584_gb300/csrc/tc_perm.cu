@@ -5,7 +5,12 @@
 // z_j[pi_k[s]] (only the second row of a pair is permuted), and
 //   counts[J(i,j)] += #{k : |r_k(i,j)| >= |r(i,j)|}       for i < j.
 //
-// Two kernels per batch of permutations:
+// perm_test dispatches to one of three forms with the same counts: the
+// transposed form (tc_perm_mn.cu, the default), the shared-memory form
+// (tc_perm_smem.cu) and the workspace form here, which also serves where
+// the other two do not apply (single CTAs, rows over 256 padded samples).
+//
+// The workspace form runs two kernels per batch of permutations:
 //   k_perm_gather  writes the permuted halves ZP[k][j][s] = Z[j][pi_k[s]]
 //                  of every row for the batch into a workspace (checking each
 //                  index: an index outside [0, l) is recorded as

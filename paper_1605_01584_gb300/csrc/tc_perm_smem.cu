@@ -41,8 +41,9 @@
 // TMA next to a resident A tile: about as many cycles of shared-memory
 // bandwidth as the stage's MMAs take, so this form can at best match the
 // workspace form (tc_perm.cu).  As built it runs well below that bound,
-// stalled on each stage's per-warp waits and hand-offs, and it serves where
-// the workspace does not fit or is not wanted.
+// stalled on each stage's per-warp waits and hand-offs.  The transposed form
+// (tc_perm_mn.cu) permutes with no shared-memory reads at all and is the
+// default; this one stays selectable.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
