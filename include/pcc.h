@@ -316,12 +316,15 @@ pcc_status pcc_edges_copy_host(const pcc_edge *edges, const uint64_t *d_count,
  *     samples): the first call after each standardize writes a transposed
  *     copy of Z (2 x lpad x n 16-bit values, kept in Z), so that the
  *     permuted column operand of a tile is a set of rows of that copy,
- *     which the kernel copies from L2 into shared memory as it goes;
+ *     which the kernel copies from L2 into shared memory as it goes.  A
+ *     call recorded by a stream capture always rebuilds the copy (a replay
+ *     may follow a later standardize).  The first call on a Z allocates
+ *     the copy: make it before capturing;
  *   - the workspace form: the permuted rows of a batch of permutations are
  *     first written to a work buffer, allocated by the first such call on a
  *     Z and kept in Z (4.2 GB for 1,000 permutations of a 4,096 x 256
- *     matrix; smaller budgets run in batches); about 1.2 times the
- *     transposed form's time;
+ *     matrix; smaller budgets run in batches; make the first call before
+ *     capturing); about 1.1 to 1.2 times the transposed form's time;
  *   - the shared-memory form (CTA pairs, rows of up to 256 padded samples):
  *     each CTA keeps 64 of the column tile's rows z_j resident in shared
  *     memory and builds every permuted operand there; no device memory is
