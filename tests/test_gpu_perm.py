@@ -121,6 +121,48 @@ def test_small_workspace_batches(pcc_gpu, tmp_path):
     assert np.array_equal(np.load(tmp_path / "g.npy"), whole)
 
 
+@pytest.mark.parametrize("prec", ["fp16x3s", "bf16x4"])
+def test_transposed_form_32_sample_stages(pcc_gpu, tmp_path, prec):
+    """The transposed form's variant with six 32-sample B stages
+    (PCC_PERM_MN_K=32, read when the library loads: a fresh process) gives
+    the workspace form's counts exactly; l = 256 runs 8 stages per pass,
+    past the ring's depth, and l = 100 a ragged last stage."""
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    for n, l, P in ((400, 256, 17), (300, 100, 6)):
+        X = synth.counts_log(n, l, seed=n + l + 71)
+        perms = synth.fisher_yates_perms(P, l, seed=l + 72)
+        before = pcc_gpu.pcc_get_tuning()
+        try:
+            pcc_gpu.pcc_set_tuning(pair_mma=1, perm_form=1)
+            ref, st, _ = gpu_perm_counts(pcc_gpu, X, perms, prec)
+        finally:
+            pcc_gpu.pcc_set_tuning(pair_mma=before["pair_mma"],
+                                   perm_form=before["perm_form"])
+        assert st == 0 and ref.max() > 0
+        np.save(tmp_path / "x.npy", X)
+        np.save(tmp_path / "p.npy", perms)
+        code = (
+            "import sys, numpy as np; sys.path[:0] = [%r, %r]\n"
+            "import test_gpu_perm as t, paper_1605_01584_gb300 as pcc\n"
+            "pcc.load()\n"
+            "got, st, _ = t.gpu_perm_counts(pcc, np.load(%r), np.load(%r),"
+            " %r)\n"
+            "assert st == 0, st\n"
+            "np.save(%r, got)\n" % (here, os.path.dirname(here),
+                                     str(tmp_path / "x.npy"),
+                                     str(tmp_path / "p.npy"), prec,
+                                     str(tmp_path / "g.npy")))
+        env = dict(os.environ, PCC_PERM_MN_K="32", PCC_PERM_FORM="2",
+                   PCC_TC_PAIR="1")
+        r = subprocess.run([sys.executable, "-c", code], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        assert np.array_equal(np.load(tmp_path / "g.npy"), ref), (n, l)
+
+
 @pytest.mark.parametrize("workspace", [0, 1, 2])
 def test_bad_permutation_index_is_reported(pcc_gpu, workspace):
     """Every form checks every index: out of range is read as sample 0 and
