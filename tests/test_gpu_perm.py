@@ -77,6 +77,31 @@ def test_identity_permutations_count_all(pcc_gpu):
     assert np.all(got[ok] == P) and np.all(got[~ok] == 0)
 
 
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_counts_past_16_bits(pcc_gpu, form):
+    """70,001 identity permutations: every unflagged pair counts all of
+    them, past the 65,535 that one 16-bit register count holds (the forms
+    add their register counts to the output at most every 65,534
+    permutations of a tile)."""
+    X = synth.counts_log(260, 16, seed=5)
+    X[7] = 1.0  # flagged row
+    P = 70001
+    perms = np.tile(np.arange(16, dtype=np.int32), (P, 1))
+    before = pcc_gpu.pcc_get_tuning()
+    try:
+        pcc_gpu.pcc_set_tuning(pair_mma=1, perm_form=form)
+        got, st, _ = gpu_perm_counts(pcc_gpu, X, perms)
+    finally:
+        pcc_gpu.pcc_set_tuning(pair_mma=before["pair_mma"],
+                               perm_form=before["perm_form"])
+    assert st == 0
+    _, flag = oracle.standardize(X)
+    I, J = np.triu_indices(260, 1)
+    ok = (flag[I] == 0) & (flag[J] == 0)
+    assert not ok.all()
+    assert np.all(got[ok] == P) and np.all(got[~ok] == 0)
+
+
 def test_split_ranges_accumulate(pcc_gpu):
     """Counting [0,a) then [a,P) adds up to counting [0,P) (resume)."""
     X = synth.counts_log(400, 128, seed=21)
